@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark: GPU Multiway Mergesort of 10^8 uint32 keys on one GB300.
+
+One step = one whole sort through the C ABI (base case, then for every merge
+round the splitter and the merge pass) of a fresh copy of the workload: a
+uniform random permutation of 0..N-1, the paper's "fully random" input
+(Sec. 6.3), N = 10^8 4-byte integers.  The input (400 MB) is larger than L2
+(129 MB), and a 400 MB device copy restores the unsorted input before every
+step, outside the timed events.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle (the
+textbook stable mergesort) on a bounded sample of the same workload instead.
+Multi-GPU runs are independent replicas (weak scaling): each rank sorts its own
+array; value = all ranks' keys / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gkeys/s at 1e8 uint32"
+UNIT = "Gkeys/s"
+DEFAULT_N = 10**8
+KEY_BYTES = 4
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "merge_pass_traffic.json")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="mms", choices=["mms", "reference"])
+    p.add_argument("--n", type=int, default=DEFAULT_N)
+    p.add_argument("--fanout", type=int, default=0, help="merge fanout K (0 = planner)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=1 << 25)
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---- clocks sampled during the timed region ---------------------------------------
+
+class ClockSampler:
+    FIELDS = ["timestamp", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={','.join(self.FIELDS)}",
+               "--format=csv,noheader,nounits", "-lms", "100"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.rows.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0: float, t1: float):
+        rows = [r for (t, r) in self.rows if t0 - 0.15 <= t <= t1 + 0.15] or [r for (_, r) in self.rows]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_uuid(dev: int) -> str:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+# ---- CPU oracle timing --------------------------------------------------------------
+
+def time_oracle(keys_np, sample: int):
+    import oracle
+    s = keys_np[:sample].copy()
+    t0 = time.perf_counter()
+    oracle.sort(s)
+    dt = time.perf_counter() - t0
+    return {"value": s.shape[0] / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {s.shape[0]} keys of the workload, single-threaded textbook stable mergesort",
+            "seconds": round(dt, 3)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import synth
+    n_sample = min(args.n, 1 << 22)
+    keys = synth.permutation(args.n if args.n <= (1 << 24) else n_sample, 1)[:n_sample]
+    import oracle
+    for _ in range(args.warmup):
+        oracle.sort(keys)
+    times = []
+    for _ in range(args.steps):
+        s = keys.copy()
+        t0 = time.perf_counter()
+        oracle.sort(s)
+        times.append(time.perf_counter() - t0)
+    sec = sum(times)
+    value = n_sample * args.steps / sec / 1e9
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": f"uniform random permutation of 0..N-1, N={args.n} uint32 (Sec. 6.3 fully random); "
+                               f"reference arm sorts a {n_sample}-key sample per step on the host",
+                   "global_batch": n_sample, "seq_len": None, "parallelism": "cpu"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n_sample} keys of the workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---- the GPU arm --------------------------------------------------------------------
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ["merge_pass.cu", "mms_common.cuh", "mms_kernels.cuh"]:
+        with open(os.path.join(ROOT, "paper_1702_07961_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(n: int):
+    """DRAM bytes per merge-pass launch from the committed ncu summary, scaled to
+    this workload; None when absent or taken on a different kernel source."""
+    try:
+        with open(PROFILE_TRAFFIC) as f:
+            p = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if p.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return p["dram_bytes_per_key"] * n
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1702_07961_gb300 as mms
+    import synth
+
+    dev = torch.device("cuda", local)
+    N = args.n
+    keys_np = synth.permutation(N, 1 + rank)
+    src = torch.from_numpy(keys_np.view(np.int32)).to(dev)
+    work = torch.empty_like(src)
+    ws = torch.zeros(mms.workspace_bytes(mms.KEY_U32, N), dtype=torch.uint8, device=dev)
+    plan = mms.plan(mms.KEY_U32, N, args.fanout)
+    n_ev = 2 + 2 * len(plan)
+    stream = torch.cuda.current_stream()
+
+    def step(events=None):
+        work.copy_(src)
+        mms.sort_keys(work, fanout=args.fanout, workspace=ws, kt=mms.KEY_U32, events=events)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    iota = torch.arange(N, dtype=torch.int64, device=dev)
+    verified = bool(torch.equal(work.to(torch.int64) & 0xFFFFFFFF, iota))
+    del iota
+    mms.workspace_status(ws)
+    if not verified:
+        raise SystemExit("bench: sorted output is wrong")
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
+    sampler = ClockSampler(gpu_uuid(local))
+    sampler.start()
+    time.sleep(0.5)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for s in range(args.steps):
+        step(evs[s])
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler.stop()
+    mms.workspace_status(ws)
+
+    step_ms = [e[0].elapsed_time(e[-1]) for e in evs]
+    stage = [[e[i].elapsed_time(e[i + 1]) for i in range(n_ev - 1)] for e in evs]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = N * world / (ms_per_step / 1e3) / 1e9
+
+    # per-kernel averages over the timed steps: [tile_sort, (splitter, merge) per round]
+    avg = [statistics.mean(s[i] for s in stage) for i in range(n_ev - 1)]
+    tile_ms = avg[0]
+    split_ms = [avg[1 + 2 * r] for r in range(len(plan))]
+    merge_ms = [avg[2 + 2 * r] for r in range(len(plan))]
+    bytes_pass = 2 * N * KEY_BYTES
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    merge_avg = statistics.mean(merge_ms) if merge_ms else None
+    totals = {"tile_sort": tile_ms, "splitter": sum(split_ms), "merge_pass": sum(merge_ms)}
+    dominant = max(totals, key=totals.get)
+    if merge_avg:
+        achieved = bytes_pass / (merge_avg / 1e3) / 1e9
+    else:
+        achieved = bytes_pass / (tile_ms / 1e3) / 1e9
+    traffic = load_traffic(N)
+    roofline = {"bound": "hbm", "kernel": "merge_pass" if merge_avg else "tile_sort",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_src, "traffic": traffic,
+                "algorithmic_bytes_per_launch": bytes_pass,
+                "per_pass_frac": [bytes_pass / (m / 1e3) / 1e9 / peak for m in merge_ms],
+                "tile_sort_frac": bytes_pass / (tile_ms / 1e3) / 1e9 / peak}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"uniform random permutation of 0..N-1, N={N} uint32 keys, key-only "
+                               "(Sec. 6.3 'fully random'), one sort per step",
+                   "global_batch": N * world, "seq_len": None, "parallelism": f"replicas{world}",
+                   "plan_fanouts": plan, "tile": mms.tile_items(mms.KEY_U32),
+                   "l2": "input 400 MB > 129 MB L2; a 400 MB copy restores the input between steps"},
+        "stages_ms": {"tile_sort": tile_ms, "splitter": split_ms, "merge_pass": merge_ms,
+                      "dominant": dominant},
+        "roofline": roofline,
+        "gpu_launches": args.steps * (1 + 2 * len(plan)),
+        "verified_vs_closed_form": verified,
+        "clocks": sampler.summary(t0, t1),
+    }
+
+    if not args.no_e2e:
+        # End to end: pinned host input -> device -> sort -> host, every step.
+        h_in = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(max(3, args.steps // 10))]
+        for i in range(len(e2e_ev) + 2):
+            a, b = e2e_ev[i % len(e2e_ev)]
+            a.record(stream)
+            work.copy_(h_in, non_blocking=True)
+            mms.sort_keys(work, fanout=args.fanout, workspace=ws, kt=mms.KEY_U32)
+            h_out.copy_(work, non_blocking=True)
+            b.record(stream)
+            if i == 1:
+                torch.cuda.synchronize()   # the first two rounds are warm-up
+        torch.cuda.synchronize()
+        e2e_ms = statistics.mean(a.elapsed_time(b) for a, b in e2e_ev)
+        ok = bool(np.array_equal(h_out.numpy().view(np.uint32)[:1000], np.arange(1000, dtype=np.uint32)))
+        out["e2e"] = {"value": N / (e2e_ms / 1e3) / 1e9 * world, "unit": UNIT,
+                      "h2d_bytes_per_step": N * KEY_BYTES, "d2h_bytes_per_step": N * KEY_BYTES,
+                      "ms_per_step": e2e_ms, "spot_check": ok}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = time_oracle(keys_np, min(args.cpu_sample, N))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,135 @@
+/*
+ * mms.h -- C ABI of the GB300 (sm_103a) GPU Multiway Mergesort library.
+ *
+ * The library sorts keys that already live in GPU memory, following the
+ * method of "An Efficient Multiway Mergesort for GPU Architectures"
+ * (Casanova, Iacono, Karsin, Sitchinava, Weichert):
+ *   - a base case that sorts fixed-size tiles on chip (Sec. 4.3),
+ *   - then ceil(log_K(N / tile)) K-way merge rounds (Sec. 4, Sec. 6.2), each
+ *     partitioned by a multi-sequence pivot search (Sec. 4.1) and merged on
+ *     chip without shared-memory bank conflicts (Sec. 4.2).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are device pointers the caller owns; they must be
+ *     16-byte aligned (any cudaMalloc / PyTorch allocation is).  `stream` is a
+ *     cudaStream_t (NULL = the legacy default stream).
+ *   - Calls are asynchronous on `stream`: they return once the work is queued.
+ *     Argument errors are reported synchronously by the return value.
+ *     Device-side errors (a bounded wait that ran out) are recorded in the
+ *     workspace status word and read back by mms_workspace_status().
+ *   - Sorting is ascending and stable: equal keys keep their input order and
+ *     32-bit values move with their keys.
+ *   - Key types: 32- and 64-bit unsigned integers (the paper's 4- and 8-byte
+ *     workloads, Sec. 6.3), and IEEE-754 binary32 ordered by totalOrder on bit
+ *     patterns (-NaN < -inf < ... < -0.0 < +0.0 < ... < +inf < +NaN, NaNs by
+ *     payload; the paper sorts integers only, so this ordering is this
+ *     library's reading).  Output bits equal input bits.
+ *   - No call throws; calls on distinct streams with distinct buffers and
+ *     workspaces may run concurrently.
+ */
+#ifndef MMS_H_
+#define MMS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MMS_OK = 0,
+  MMS_ERR_INVALID_ARG = 1,  /* null/misaligned pointer, size mismatch, bad fanout */
+  MMS_ERR_UNSUPPORTED = 2,  /* key type / entry point combination not provided */
+  MMS_ERR_NO_MEMORY = 3,    /* workspace too small, or internal allocation failed */
+  MMS_ERR_CUDA = 4,         /* a CUDA runtime call failed; see mms_last_error_detail */
+  MMS_ERR_TIMEOUT = 5,      /* a device-side bounded wait ran out */
+  MMS_ERR_INTERNAL = 6      /* a device-side consistency check failed */
+} mms_status;
+
+typedef enum { MMS_KEY_U32 = 0, MMS_KEY_U64 = 1, MMS_KEY_F32 = 2 } mms_key_type;
+
+/* Planner overrides and a profiling hook; a NULL pointer or zero fields mean
+ * "planner's choice, no hook". */
+typedef struct {
+  int fanout;        /* K of every merge round, 2..32 (Sec. 6.2: K is tuned per platform) */
+  int num_events;    /* entries of `events` */
+  void** events;     /* cudaEvent_t handles the caller created: events[0] is recorded on
+                        `stream` before the first kernel, events[i] after the i-th kernel
+                        (base case, then splitter and merge pass of each round), while
+                        i < num_events.  Lets a caller time every step of the real call. */
+  int reserved[4];
+} mms_options;
+
+/* Bytes of workspace mms_sort_keys / mms_sort_pairs need for n keys: one
+ * ping-pong copy of the keys (and values), the pivot table of the largest
+ * round, and a status word. */
+size_t mms_sort_workspace_bytes(mms_key_type kt, size_t n, int with_values);
+
+/* Sorts n keys of type kt at d_keys in place (from the caller's view).
+ * d_ws: workspace of at least mms_sort_workspace_bytes(kt, n, 0) bytes, or
+ * NULL to let the library allocate one stream-ordered (cudaMallocAsync) and
+ * free it after the sort.  n = 0 and n = 1 are no-ops. */
+mms_status mms_sort_keys(mms_key_type kt, void* d_keys, size_t n, void* d_ws, size_t ws_bytes,
+                         void* stream);
+mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws, size_t ws_bytes,
+                            void* stream, const mms_options* opt);
+
+/* Sorts (key, 32-bit value) pairs stably by key; values move with keys.
+ * Workspace: mms_sort_workspace_bytes(kt, n, 1). */
+mms_status mms_sort_pairs(mms_key_type kt, void* d_keys, uint32_t* d_values, size_t n, void* d_ws,
+                          size_t ws_bytes, void* stream);
+
+/* Reads (synchronising with `stream`) and clears the workspace status word:
+ * MMS_OK, MMS_ERR_TIMEOUT or MMS_ERR_INTERNAL. */
+mms_status mms_workspace_status(void* d_ws, size_t ws_bytes, void* stream);
+
+/* ---- the hot-path steps one by one (for parity tests and profiling) -------- */
+
+/* Items per base-case tile and per merge output tile for key type kt
+ * (8192 for 4-byte keys, 4096 for 8-byte keys). */
+size_t mms_tile_items(mms_key_type kt);
+
+/* Plan of a sort: number of merge rounds and the fanout of each (up to 16
+ * entries written to fanouts).  Returns the number of rounds. */
+int mms_plan(mms_key_type kt, size_t n, const mms_options* opt, int* fanouts, int max_rounds);
+
+/* Base case (Sec. 4.3): sorts every tile of mms_tile_items(kt) consecutive
+ * keys of d_in into d_out (d_in == d_out allowed).  The last tile may be
+ * short.  Float keys are sorted by totalOrder and written back as floats. */
+mms_status mms_tile_sort(mms_key_type kt, const void* d_in, void* d_out, size_t n, void* stream);
+
+/* Number of rows of the pivot table of a merge round over n keys in sorted
+ * runs of run_len keys merged K at a time: one row per output tile. */
+size_t mms_splitter_rows(mms_key_type kt, size_t n, size_t run_len, int K);
+
+/* Parallel partitioning (Sec. 4.1): d_in holds sorted runs of run_len keys
+ * (the last one may be short; run_len a multiple of mms_tile_items(kt)).
+ * Groups of K consecutive runs are merged into one; for output tile j of a
+ * group, row t of d_table (K int64 entries, rows in tile order, group after
+ * group) receives, for each run r of the group, the number of its keys among
+ * the group's first j * mms_tile_items(kt) outputs under the strict order
+ * (key, run, position).  Integer key types only (u32, u64). */
+mms_status mms_splitter(mms_key_type kt, const void* d_in, size_t n, size_t run_len, int K,
+                        int64_t* d_table, void* stream);
+
+/* One K-way merge round (Sec. 4.2): merges every group of K runs of d_in into
+ * one sorted run of d_out, driven by the table mms_splitter wrote for the
+ * same (d_in, n, run_len, K).  d_in and d_out must not overlap.  d_ws: NULL,
+ * or a sort workspace whose status word records device-side errors.
+ * Integer key types only. */
+mms_status mms_merge_pass(mms_key_type kt, const void* d_in, void* d_out, size_t n,
+                          size_t run_len, int K, const int64_t* d_table, void* d_ws,
+                          size_t ws_bytes, void* stream);
+
+/* ---- diagnostics ----------------------------------------------------------- */
+
+const char* mms_status_string(mms_status s);
+/* Copies the detail of the last failing call on this host thread into buf. */
+mms_status mms_last_error_detail(char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MMS_H_ */

@@ -1,0 +1,202 @@
+"""GB300-native GPU Multiway Mergesort (Casanova, Iacono, Karsin, Sitchinava,
+Weichert, "An Efficient Multiway Mergesort for GPU Architectures").
+
+A thin Python binding over ``libmms.so`` (C ABI in ``include/mms.h``): it only
+marshals arguments.  Every step of the sort runs in the library's CUDA kernels;
+PyTorch provides device memory and streams.  There is no CPU fallback: when the
+library has not been built, :func:`load` raises.
+
+Keys: ``torch.uint32``/``torch.int32`` tensors are sorted as unsigned 32-bit
+integers, ``torch.uint64``/``torch.int64`` as unsigned 64-bit integers,
+``torch.float32`` by IEEE-754 totalOrder on bit patterns.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = ["load", "KEY_U32", "KEY_U64", "KEY_F32", "key_type_of", "sort_keys", "sort_pairs",
+           "workspace_bytes", "tile_items", "plan", "tile_sort", "splitter_rows", "splitter",
+           "merge_pass", "workspace_status", "MMSError"]
+
+KEY_U32, KEY_U64, KEY_F32 = 0, 1, 2
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "_build", "libmms.so")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MMSError(RuntimeError):
+    def __init__(self, status: int, detail: str):
+        super().__init__(f"mms status {status}: {detail}")
+        self.status = status
+        self.detail = detail
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("fanout", ctypes.c_int), ("num_events", ctypes.c_int),
+                ("events", ctypes.POINTER(ctypes.c_void_p)), ("reserved", ctypes.c_int * 4)]
+
+
+def load() -> ctypes.CDLL:
+    """Loads libmms.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(SO_PATH):
+            raise FileNotFoundError(
+                f"{SO_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(SO_PATH)
+        vp, sz, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+        L.mms_sort_workspace_bytes.argtypes = [i32, sz, i32]
+        L.mms_sort_workspace_bytes.restype = sz
+        L.mms_sort_keys.argtypes = [i32, vp, sz, vp, sz, vp]
+        L.mms_sort_keys.restype = i32
+        L.mms_sort_keys_ex.argtypes = [i32, vp, sz, vp, sz, vp, ctypes.POINTER(_Options)]
+        L.mms_sort_keys_ex.restype = i32
+        L.mms_sort_pairs.argtypes = [i32, vp, vp, sz, vp, sz, vp]
+        L.mms_sort_pairs.restype = i32
+        L.mms_workspace_status.argtypes = [vp, sz, vp]
+        L.mms_workspace_status.restype = i32
+        L.mms_tile_items.argtypes = [i32]
+        L.mms_tile_items.restype = sz
+        L.mms_plan.argtypes = [i32, sz, ctypes.POINTER(_Options), ctypes.POINTER(ctypes.c_int), i32]
+        L.mms_plan.restype = i32
+        L.mms_tile_sort.argtypes = [i32, vp, vp, sz, vp]
+        L.mms_tile_sort.restype = i32
+        L.mms_splitter_rows.argtypes = [i32, sz, sz, i32]
+        L.mms_splitter_rows.restype = sz
+        L.mms_splitter.argtypes = [i32, vp, sz, sz, i32, vp, vp]
+        L.mms_splitter.restype = i32
+        L.mms_merge_pass.argtypes = [i32, vp, vp, sz, sz, i32, vp, vp, sz, vp]
+        L.mms_merge_pass.restype = i32
+        L.mms_status_string.argtypes = [i32]
+        L.mms_status_string.restype = ctypes.c_char_p
+        L.mms_last_error_detail.argtypes = [ctypes.c_char_p, sz]
+        L.mms_last_error_detail.restype = i32
+        _lib = L
+        return L
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        L = load()
+        buf = ctypes.create_string_buffer(256)
+        L.mms_last_error_detail(buf, 256)
+        raise MMSError(status, f"{L.mms_status_string(status).decode()}: {buf.value.decode()}")
+
+
+def key_type_of(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return KEY_F32
+    if t.dtype in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        return KEY_U32
+    if t.dtype in (torch.int64, getattr(torch, "uint64", torch.int64)):
+        return KEY_U64
+    raise TypeError(f"unsupported key dtype {t.dtype}")
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _opts(fanout: int, events=None, stream=None):
+    o = _Options()
+    o.fanout = int(fanout)
+    if events:
+        for e in events:
+            if not e.cuda_event:          # torch creates the CUDA event on first record
+                e.record(stream)
+        arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
+        o.num_events = len(events)
+        o.events = ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
+        o._keep = arr
+    return o
+
+
+def workspace_bytes(kt: int, n: int, with_values: bool = False) -> int:
+    return int(load().mms_sort_workspace_bytes(kt, n, int(with_values)))
+
+
+def tile_items(kt: int) -> int:
+    return int(load().mms_tile_items(kt))
+
+
+def plan(kt: int, n: int, fanout: int = 0):
+    buf = (ctypes.c_int * 64)()
+    o = _opts(fanout)
+    r = load().mms_plan(kt, n, ctypes.byref(o), buf, 64)
+    return [buf[i] for i in range(r)]
+
+
+def sort_keys(keys, fanout: int = 0, workspace=None, stream=None, kt: int | None = None, events=None):
+    """Sorts a contiguous CUDA tensor of keys in place; returns it.
+
+    ``events``: optional list of ``torch.cuda.Event(enable_timing=True)``; the
+    library records them before the first kernel and after each kernel.
+    """
+    assert keys.is_cuda and keys.is_contiguous()
+    kt = key_type_of(keys) if kt is None else kt
+    n = keys.numel()
+    ws_ptr, ws_len = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
+    o = _opts(fanout, events, stream)
+    _check(load().mms_sort_keys_ex(kt, _ptr(keys), n, ws_ptr, ws_len, _stream_handle(stream), ctypes.byref(o)))
+    return keys
+
+
+def sort_pairs(keys, values, workspace=None, stream=None, kt: int | None = None):
+    """Stable sort of (key, 32-bit value) pairs in place."""
+    assert keys.is_cuda and values.is_cuda and keys.numel() == values.numel()
+    kt = key_type_of(keys) if kt is None else kt
+    ws_ptr, ws_len = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
+    _check(load().mms_sort_pairs(kt, _ptr(keys), _ptr(values), keys.numel(), ws_ptr, ws_len,
+                                 _stream_handle(stream)))
+    return keys, values
+
+
+def workspace_status(workspace, stream=None) -> None:
+    """Raises MMSError if a kernel recorded a device-side error in the workspace."""
+    _check(load().mms_workspace_status(_ptr(workspace), workspace.numel() * workspace.element_size(),
+                                       _stream_handle(stream)))
+
+
+def tile_sort(inp, out=None, stream=None, kt: int | None = None):
+    """Base case: sorts every tile of tile_items(kt) keys of ``inp`` into ``out``."""
+    kt = key_type_of(inp) if kt is None else kt
+    out = inp if out is None else out
+    _check(load().mms_tile_sort(kt, _ptr(inp), _ptr(out), inp.numel(), _stream_handle(stream)))
+    return out
+
+
+def splitter_rows(kt: int, n: int, run_len: int, K: int) -> int:
+    return int(load().mms_splitter_rows(kt, n, run_len, K))
+
+
+def splitter(data, run_len: int, K: int, table=None, stream=None, kt: int | None = None):
+    """Pivot table of a merge round (rows x K int64 tensor on the device)."""
+    import torch
+    kt = key_type_of(data) if kt is None else kt
+    rows = splitter_rows(kt, data.numel(), run_len, K)
+    if table is None:
+        table = torch.empty((rows, K), dtype=torch.int64, device=data.device)
+    _check(load().mms_splitter(kt, _ptr(data), data.numel(), run_len, K, _ptr(table), _stream_handle(stream)))
+    return table
+
+
+def merge_pass(inp, out, run_len: int, K: int, table, workspace=None, stream=None, kt: int | None = None):
+    """One K-way merge round of ``inp`` into ``out`` driven by ``table``."""
+    kt = key_type_of(inp) if kt is None else kt
+    ws_ptr, ws_len = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
+    _check(load().mms_merge_pass(kt, _ptr(inp), _ptr(out), inp.numel(), run_len, K, _ptr(table),
+                                 ws_ptr, ws_len, _stream_handle(stream)))
+    return out

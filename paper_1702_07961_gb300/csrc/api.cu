@@ -1,0 +1,271 @@
+// api.cu -- the C ABI declared in include/mms.h: argument checks, the planner
+// (base-case tile and per-round fanout, Sec. 6.2), the workspace layout, and
+// the launch sequence of one sort: base case, then for every merge round the
+// splitter and the merge pass, ping-ponging between the caller's buffer and
+// the workspace copy so that the last round lands in the caller's buffer.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/mms.h"
+#include "mms_kernels.cuh"
+
+namespace {
+
+thread_local char g_detail[256] = "";
+
+mms_status fail(mms_status s, const char* fmt, const char* what = "") {
+  snprintf(g_detail, sizeof g_detail, fmt, what);
+  return s;
+}
+
+mms_status cuda_fail(cudaError_t e, const char* where) {
+  snprintf(g_detail, sizeof g_detail, "%s: %s", where, cudaGetErrorString(e));
+  return MMS_ERR_CUDA;
+}
+
+int key_bytes_of(mms_key_type kt) { return kt == MMS_KEY_U64 ? 8 : 4; }
+bool valid_kt(int kt) { return kt == MMS_KEY_U32 || kt == MMS_KEY_U64 || kt == MMS_KEY_F32; }
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+constexpr size_t kStatusBytes = 256;
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct WsLayout {
+  size_t keys_off, vals_off, table_off, total;
+};
+
+WsLayout ws_layout(mms_key_type kt, size_t n, int with_values) {
+  WsLayout L;
+  const size_t kb = (size_t)key_bytes_of(kt);
+  const size_t S = (size_t)mms::tile_items(key_bytes_of(kt));
+  L.keys_off = kStatusBytes;
+  L.vals_off = round_up(L.keys_off + n * kb, 256);
+  const size_t after_vals = L.vals_off + (with_values ? n * 4 : 0);
+  L.table_off = round_up(after_vals, 256);
+  const size_t rows = (n + S - 1) / S + 1;
+  L.total = round_up(L.table_off + rows * mms::kMaxFanout * sizeof(long long), 256);
+  return L;
+}
+
+// Fanout of every round.  Auto: as few rounds as K <= 32 allows, with the
+// log2 K levels spread evenly (Sec. 6.2 avoids a last round merging fewer
+// than K lists by resizing the base case; spreading the levels serves the
+// same end without changing the tile).
+int plan_rounds(int key_bytes, size_t n, const mms_options* opt, int* K, int maxr) {
+  const long long S = mms::tile_items(key_bytes);
+  const long long runs = ((long long)n + S - 1) / S;
+  if (runs <= 1) return 0;
+  int levels = 0;
+  while ((1ll << levels) < runs) ++levels;
+  int rounds = 0;
+  if (opt && opt->fanout >= 2) {
+    long long cover = 1;
+    while (cover < runs) {
+      cover *= opt->fanout;
+      if (rounds < maxr) K[rounds] = opt->fanout;
+      ++rounds;
+    }
+    return rounds;
+  }
+  rounds = (levels + 4) / 5;
+  const int base = levels / rounds, extra = levels % rounds;
+  for (int i = 0; i < rounds && i < maxr; ++i) K[i] = 1 << (base + (i < extra ? 1 : 0));
+  return rounds;
+}
+
+mms_status check_launch(cudaError_t e, const char* where) {
+  return e == cudaSuccess ? MMS_OK : cuda_fail(e, where);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mms_status_string(mms_status s) {
+  switch (s) {
+    case MMS_OK: return "ok";
+    case MMS_ERR_INVALID_ARG: return "invalid argument";
+    case MMS_ERR_UNSUPPORTED: return "unsupported";
+    case MMS_ERR_NO_MEMORY: return "out of memory / workspace too small";
+    case MMS_ERR_CUDA: return "CUDA error";
+    case MMS_ERR_TIMEOUT: return "device-side wait timed out";
+    case MMS_ERR_INTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+mms_status mms_last_error_detail(char* buf, size_t len) {
+  if (!buf || len == 0) return MMS_ERR_INVALID_ARG;
+  snprintf(buf, len, "%s", g_detail);
+  return MMS_OK;
+}
+
+size_t mms_tile_items(mms_key_type kt) {
+  return valid_kt(kt) ? (size_t)mms::tile_items(key_bytes_of(kt)) : 0;
+}
+
+size_t mms_sort_workspace_bytes(mms_key_type kt, size_t n, int with_values) {
+  if (!valid_kt(kt)) return 0;
+  return ws_layout(kt, n, with_values).total;
+}
+
+int mms_plan(mms_key_type kt, size_t n, const mms_options* opt, int* fanouts, int max_rounds) {
+  if (!valid_kt(kt)) return -1;
+  int K[64];
+  const int r = plan_rounds(key_bytes_of(kt), n, opt, K, 64);
+  for (int i = 0; i < r && i < max_rounds && fanouts; ++i) fanouts[i] = K[i];
+  return r;
+}
+
+mms_status mms_workspace_status(void* d_ws, size_t ws_bytes, void* stream) {
+  if (!d_ws || ws_bytes < kStatusBytes) return fail(MMS_ERR_INVALID_ARG, "workspace missing%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  int word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, d_ws, sizeof word, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && word != 0) e = cudaMemsetAsync(d_ws, 0, sizeof word, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "mms_workspace_status");
+  if (word == mms::kDevErrTimeout) return fail(MMS_ERR_TIMEOUT, "a device wait timed out%s");
+  if (word != 0) return fail(MMS_ERR_INTERNAL, "device consistency check failed%s");
+  return MMS_OK;
+}
+
+mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws, size_t ws_bytes,
+                            void* stream, const mms_options* opt) {
+  if (!valid_kt(kt)) return fail(MMS_ERR_INVALID_ARG, "unknown key type%s");
+  if (n <= 1) return MMS_OK;
+  if (!d_keys || !aligned16(d_keys)) return fail(MMS_ERR_INVALID_ARG, "keys pointer null or not 16-byte aligned%s");
+  if (opt && opt->fanout != 0 && (opt->fanout < 2 || opt->fanout > mms::kMaxFanout))
+    return fail(MMS_ERR_INVALID_ARG, "fanout must be 0 or in 2..32%s");
+  const int kb = key_bytes_of(kt);
+  const WsLayout L = ws_layout(kt, n, 0);
+  cudaStream_t s = (cudaStream_t)stream;
+  bool owned = false;
+  if (d_ws) {
+    if (!aligned16(d_ws)) return fail(MMS_ERR_INVALID_ARG, "workspace not 16-byte aligned%s");
+    if (ws_bytes < L.total) return fail(MMS_ERR_NO_MEMORY, "workspace smaller than mms_sort_workspace_bytes()%s");
+  } else {
+    cudaError_t e = cudaMallocAsync(&d_ws, L.total, s);
+    if (e != cudaSuccess) return fail(MMS_ERR_NO_MEMORY, "cudaMallocAsync of the workspace failed%s");
+    e = cudaMemsetAsync(d_ws, 0, kStatusBytes, s);
+    if (e != cudaSuccess) { cudaFreeAsync(d_ws, s); return cuda_fail(e, "workspace init"); }
+    owned = true;
+  }
+  unsigned char* ws = static_cast<unsigned char*>(d_ws);
+  int* dev_err = reinterpret_cast<int*>(ws);
+  void* tmp = ws + L.keys_off;
+  long long* table = reinterpret_cast<long long*>(ws + L.table_off);
+
+  int K[64];
+  const int rounds = plan_rounds(kb, n, opt, K, 64);
+  const bool is_f32 = kt == MMS_KEY_F32;
+  mms_status st = MMS_OK;
+  // Base case writes to the caller's buffer when an even number of rounds follows.
+  void* cur = (rounds % 2 == 1) ? tmp : d_keys;
+  void* other = (cur == tmp) ? d_keys : tmp;
+  int ev = 0;
+  auto mark = [&]() {
+    if (opt && opt->events && ev < opt->num_events && opt->events[ev])
+      cudaEventRecord((cudaEvent_t)opt->events[ev], s);
+    ++ev;
+  };
+  mark();
+  st = check_launch(mms::launch_tile_sort(kb, is_f32, is_f32 && rounds == 0, d_keys, cur,
+                                          (long long)n, s), "tile_sort");
+  mark();
+  long long run_len = mms::tile_items(kb);
+  for (int r = 0; r < rounds && st == MMS_OK; ++r) {
+    st = check_launch(mms::launch_splitter(kb, cur, (long long)n, run_len, K[r], table, s), "splitter");
+    mark();
+    if (st != MMS_OK) break;
+    st = check_launch(mms::launch_merge_pass(kb, is_f32 && r == rounds - 1, cur, other, (long long)n,
+                                             run_len, K[r], table, dev_err, s), "merge_pass");
+    mark();
+    void* t = cur;
+    cur = other;
+    other = t;
+    run_len *= K[r];
+  }
+  if (owned) {
+    // A device-side error would be lost with the workspace: surface it now.
+    int word = 0;
+    cudaError_t e = cudaMemcpyAsync(&word, dev_err, sizeof word, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d_ws, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (st == MMS_OK && e != cudaSuccess) st = cuda_fail(e, "sort");
+    if (st == MMS_OK && word == mms::kDevErrTimeout) st = fail(MMS_ERR_TIMEOUT, "a device wait timed out%s");
+    else if (st == MMS_OK && word != 0) st = fail(MMS_ERR_INTERNAL, "device consistency check failed%s");
+  }
+  return st;
+}
+
+mms_status mms_sort_keys(mms_key_type kt, void* d_keys, size_t n, void* d_ws, size_t ws_bytes,
+                         void* stream) {
+  return mms_sort_keys_ex(kt, d_keys, n, d_ws, ws_bytes, stream, nullptr);
+}
+
+mms_status mms_sort_pairs(mms_key_type kt, void* d_keys, uint32_t* d_values, size_t n, void* d_ws,
+                          size_t ws_bytes, void* stream) {
+  (void)kt; (void)d_keys; (void)d_values; (void)n; (void)d_ws; (void)ws_bytes; (void)stream;
+  return fail(MMS_ERR_UNSUPPORTED, "key-value sorting is not built yet%s");
+}
+
+mms_status mms_tile_sort(mms_key_type kt, const void* d_in, void* d_out, size_t n, void* stream) {
+  if (!valid_kt(kt)) return fail(MMS_ERR_INVALID_ARG, "unknown key type%s");
+  if (n == 0) return MMS_OK;
+  if (!d_in || !d_out || !aligned16(d_in) || !aligned16(d_out))
+    return fail(MMS_ERR_INVALID_ARG, "buffers null or not 16-byte aligned%s");
+  const bool f = kt == MMS_KEY_F32;
+  return check_launch(mms::launch_tile_sort(key_bytes_of(kt), f, f, d_in, d_out, (long long)n,
+                                            (cudaStream_t)stream), "tile_sort");
+}
+
+size_t mms_splitter_rows(mms_key_type kt, size_t n, size_t run_len, int K) {
+  if (!valid_kt(kt) || K < 2 || run_len == 0) return 0;
+  return (size_t)mms::num_tiles(key_bytes_of(kt), (long long)n, (long long)run_len, K);
+}
+
+static mms_status check_round_args(mms_key_type kt, size_t run_len, int K) {
+  if (kt != MMS_KEY_U32 && kt != MMS_KEY_U64)
+    return fail(MMS_ERR_UNSUPPORTED, "merge-round steps take integer keys only%s");
+  if (K < 2 || K > mms::kMaxFanout) return fail(MMS_ERR_INVALID_ARG, "K must be in 2..32%s");
+  const size_t S = (size_t)mms::tile_items(key_bytes_of(kt));
+  if (run_len == 0 || run_len % S != 0)
+    return fail(MMS_ERR_INVALID_ARG, "run_len must be a positive multiple of the tile size%s");
+  return MMS_OK;
+}
+
+mms_status mms_splitter(mms_key_type kt, const void* d_in, size_t n, size_t run_len, int K,
+                        int64_t* d_table, void* stream) {
+  mms_status st = check_round_args(kt, run_len, K);
+  if (st != MMS_OK) return st;
+  if (n == 0) return MMS_OK;
+  if (!d_in || !d_table || !aligned16(d_in)) return fail(MMS_ERR_INVALID_ARG, "null or misaligned buffer%s");
+  return check_launch(mms::launch_splitter(key_bytes_of(kt), d_in, (long long)n, (long long)run_len,
+                                           K, reinterpret_cast<long long*>(d_table),
+                                           (cudaStream_t)stream), "splitter");
+}
+
+mms_status mms_merge_pass(mms_key_type kt, const void* d_in, void* d_out, size_t n,
+                          size_t run_len, int K, const int64_t* d_table, void* d_ws,
+                          size_t ws_bytes, void* stream) {
+  mms_status st = check_round_args(kt, run_len, K);
+  if (st != MMS_OK) return st;
+  if (n == 0) return MMS_OK;
+  if (!d_in || !d_out || !d_table || !aligned16(d_in) || !aligned16(d_out))
+    return fail(MMS_ERR_INVALID_ARG, "null or misaligned buffer%s");
+  const size_t kb = (size_t)key_bytes_of(kt);
+  const char* a = static_cast<const char*>(d_in);
+  const char* b = static_cast<const char*>(d_out);
+  if (a < b + n * kb && b < a + n * kb) return fail(MMS_ERR_INVALID_ARG, "input and output overlap%s");
+  if (d_ws && ws_bytes < kStatusBytes) return fail(MMS_ERR_INVALID_ARG, "workspace too small%s");
+  int* dev_err = d_ws ? static_cast<int*>(d_ws) : nullptr;
+  return check_launch(mms::launch_merge_pass((int)kb, false, d_in, d_out, (long long)n,
+                                             (long long)run_len, K,
+                                             reinterpret_cast<const long long*>(d_table), dev_err,
+                                             (cudaStream_t)stream), "merge_pass");
+}
+
+}  // extern "C"
