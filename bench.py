@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--impl", default="mms", choices=["mms", "reference"])
     p.add_argument("--n", type=int, default=DEFAULT_N)
     p.add_argument("--fanout", type=int, default=0, help="merge fanout K (0 = planner)")
+    p.add_argument("--tile", type=int, default=0, help="tile items (0 = library default)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=1 << 25)
@@ -216,13 +217,14 @@ def main():
     src = torch.from_numpy(keys_np.view(np.int32)).to(dev)
     work = torch.empty_like(src)
     ws = torch.zeros(mms.workspace_bytes(mms.KEY_U32, N), dtype=torch.uint8, device=dev)
-    plan = mms.plan(mms.KEY_U32, N, args.fanout)
+    plan = mms.plan(mms.KEY_U32, N, args.fanout, args.tile)
     n_ev = 2 + 2 * len(plan)
     stream = torch.cuda.current_stream()
 
     def step(events=None):
         work.copy_(src)
-        mms.sort_keys(work, fanout=args.fanout, workspace=ws, kt=mms.KEY_U32, events=events)
+        mms.sort_keys(work, fanout=args.fanout, workspace=ws, kt=mms.KEY_U32, events=events,
+                      tile_items=args.tile)
 
     for _ in range(args.warmup):
         step()
@@ -298,7 +300,7 @@ def main():
         "config": {"workload": f"uniform random permutation of 0..N-1, N={N} uint32 keys, key-only "
                                "(Sec. 6.3 'fully random'), one sort per step",
                    "global_batch": N * world, "seq_len": None, "parallelism": f"replicas{world}",
-                   "plan_fanouts": plan, "tile": mms.tile_items(mms.KEY_U32),
+                   "plan_fanouts": plan, "tile": args.tile or mms.tile_items(mms.KEY_U32),
                    "l2": "input 400 MB > 129 MB L2; a 400 MB copy restores the input between steps"},
         "stages_ms": {"tile_sort": tile_ms, "splitter": split_ms, "merge_pass": merge_ms,
                       "dominant": dominant},
@@ -318,7 +320,7 @@ def main():
             a, b = e2e_ev[i % len(e2e_ev)]
             a.record(stream)
             work.copy_(h_in, non_blocking=True)
-            mms.sort_keys(work, fanout=args.fanout, workspace=ws, kt=mms.KEY_U32)
+            mms.sort_keys(work, fanout=args.fanout, workspace=ws, kt=mms.KEY_U32, tile_items=args.tile)
             h_out.copy_(work, non_blocking=True)
             b.record(stream)
             if i == 1:

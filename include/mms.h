@@ -58,7 +58,9 @@ typedef struct {
                         `stream` before the first kernel, events[i] after the i-th kernel
                         (base case, then splitter and merge pass of each round), while
                         i < num_events.  Lets a caller time every step of the real call. */
-  int reserved[4];
+  int tile_items;    /* base-case / merge tile: 0 = mms_tile_items(kt); else 4096 or 8192
+                        for 4-byte keys, 2048 or 4096 for 8-byte keys */
+  int reserved[3];
 } mms_options;
 
 /* Bytes of workspace mms_sort_keys / mms_sort_pairs need for n keys: one

@@ -38,7 +38,7 @@ struct WsLayout {
 WsLayout ws_layout(mms_key_type kt, size_t n, int with_values) {
   WsLayout L;
   const size_t kb = (size_t)key_bytes_of(kt);
-  const size_t S = (size_t)mms::tile_items(key_bytes_of(kt));
+  const size_t S = (kb == 8 ? 2048 : 4096);      // smallest tile a sort may use
   L.keys_off = kStatusBytes;
   L.vals_off = round_up(L.keys_off + n * kb, 256);
   const size_t after_vals = L.vals_off + (with_values ? n * 4 : 0);
@@ -48,12 +48,18 @@ WsLayout ws_layout(mms_key_type kt, size_t n, int with_values) {
   return L;
 }
 
+// Tile width (warps per CTA, 1024 items each) a sort uses.
+int tile_warps_for(int key_bytes, const mms_options* opt) {
+  if (opt && opt->tile_items > 0) return opt->tile_items / 1024;
+  return mms::default_tile_warps(key_bytes);
+}
+
 // Fanout of every round.  Auto: as few rounds as K <= 32 allows, with the
 // log2 K levels spread evenly (Sec. 6.2 avoids a last round merging fewer
 // than K lists by resizing the base case; spreading the levels serves the
 // same end without changing the tile).
 int plan_rounds(int key_bytes, size_t n, const mms_options* opt, int* K, int maxr) {
-  const long long S = mms::tile_items(key_bytes);
+  const long long S = 1024ll * tile_warps_for(key_bytes, opt);
   const long long runs = ((long long)n + S - 1) / S;
   if (runs <= 1) return 0;
   int levels = 0;
@@ -102,7 +108,7 @@ mms_status mms_last_error_detail(char* buf, size_t len) {
 }
 
 size_t mms_tile_items(mms_key_type kt) {
-  return valid_kt(kt) ? (size_t)mms::tile_items(key_bytes_of(kt)) : 0;
+  return valid_kt(kt) ? (size_t)1024 * mms::default_tile_warps(key_bytes_of(kt)) : 0;
 }
 
 size_t mms_sort_workspace_bytes(mms_key_type kt, size_t n, int with_values) {
@@ -140,6 +146,11 @@ mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws,
   if (opt && opt->fanout != 0 && (opt->fanout < 2 || opt->fanout > mms::kMaxFanout))
     return fail(MMS_ERR_INVALID_ARG, "fanout must be 0 or in 2..32%s");
   const int kb = key_bytes_of(kt);
+  if (opt && opt->tile_items != 0 &&
+      (opt->tile_items % 1024 != 0 || !mms::valid_tile_warps(kb, opt->tile_items / 1024)))
+    return fail(MMS_ERR_INVALID_ARG, "tile_items must be 0, 4096/8192 (4-byte keys) or 2048/4096 (8-byte keys)%s");
+  const int tw = tile_warps_for(kb, opt);
+  const long long S = 1024ll * tw;
   const WsLayout L = ws_layout(kt, n, 0);
   cudaStream_t s = (cudaStream_t)stream;
   bool owned = false;
@@ -172,16 +183,17 @@ mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws,
     ++ev;
   };
   mark();
-  st = check_launch(mms::launch_tile_sort(kb, is_f32, is_f32 && rounds == 0, d_keys, cur,
+  st = check_launch(mms::launch_tile_sort(kb, tw, is_f32, is_f32 && rounds == 0, d_keys, cur,
                                           (long long)n, s), "tile_sort");
   mark();
-  long long run_len = mms::tile_items(kb);
+  long long run_len = S;
   for (int r = 0; r < rounds && st == MMS_OK; ++r) {
-    st = check_launch(mms::launch_splitter(kb, cur, (long long)n, run_len, K[r], table, s), "splitter");
+    st = check_launch(mms::launch_splitter(kb, S, cur, (long long)n, run_len, K[r], table, s), "splitter");
     mark();
     if (st != MMS_OK) break;
-    st = check_launch(mms::launch_merge_pass(kb, is_f32 && r == rounds - 1, cur, other, (long long)n,
-                                             run_len, K[r], table, dev_err, s), "merge_pass");
+    st = check_launch(mms::launch_merge_pass(kb, tw, is_f32 && r == rounds - 1, cur, other,
+                                             (long long)n, run_len, K[r], table, dev_err, s),
+                      "merge_pass");
     mark();
     void* t = cur;
     cur = other;
@@ -218,20 +230,23 @@ mms_status mms_tile_sort(mms_key_type kt, const void* d_in, void* d_out, size_t 
   if (!d_in || !d_out || !aligned16(d_in) || !aligned16(d_out))
     return fail(MMS_ERR_INVALID_ARG, "buffers null or not 16-byte aligned%s");
   const bool f = kt == MMS_KEY_F32;
-  return check_launch(mms::launch_tile_sort(key_bytes_of(kt), f, f, d_in, d_out, (long long)n,
+  const int kb = key_bytes_of(kt);
+  return check_launch(mms::launch_tile_sort(kb, mms::default_tile_warps(kb), f, f, d_in, d_out, (long long)n,
                                             (cudaStream_t)stream), "tile_sort");
 }
 
 size_t mms_splitter_rows(mms_key_type kt, size_t n, size_t run_len, int K) {
   if (!valid_kt(kt) || K < 2 || run_len == 0) return 0;
-  return (size_t)mms::num_tiles(key_bytes_of(kt), (long long)n, (long long)run_len, K);
+  const long long S = 1024ll * mms::default_tile_warps(key_bytes_of(kt));
+  if (run_len % S != 0) return 0;
+  return (size_t)mms::num_tiles(S, (long long)n, (long long)run_len, K);
 }
 
 static mms_status check_round_args(mms_key_type kt, size_t run_len, int K) {
   if (kt != MMS_KEY_U32 && kt != MMS_KEY_U64)
     return fail(MMS_ERR_UNSUPPORTED, "merge-round steps take integer keys only%s");
   if (K < 2 || K > mms::kMaxFanout) return fail(MMS_ERR_INVALID_ARG, "K must be in 2..32%s");
-  const size_t S = (size_t)mms::tile_items(key_bytes_of(kt));
+  const size_t S = (size_t)1024 * mms::default_tile_warps(key_bytes_of(kt));
   if (run_len == 0 || run_len % S != 0)
     return fail(MMS_ERR_INVALID_ARG, "run_len must be a positive multiple of the tile size%s");
   return MMS_OK;
@@ -243,7 +258,9 @@ mms_status mms_splitter(mms_key_type kt, const void* d_in, size_t n, size_t run_
   if (st != MMS_OK) return st;
   if (n == 0) return MMS_OK;
   if (!d_in || !d_table || !aligned16(d_in)) return fail(MMS_ERR_INVALID_ARG, "null or misaligned buffer%s");
-  return check_launch(mms::launch_splitter(key_bytes_of(kt), d_in, (long long)n, (long long)run_len,
+  const int kb = key_bytes_of(kt);
+  return check_launch(mms::launch_splitter(kb, 1024ll * mms::default_tile_warps(kb), d_in, (long long)n,
+                                           (long long)run_len,
                                            K, reinterpret_cast<long long*>(d_table),
                                            (cudaStream_t)stream), "splitter");
 }
@@ -262,7 +279,8 @@ mms_status mms_merge_pass(mms_key_type kt, const void* d_in, void* d_out, size_t
   if (a < b + n * kb && b < a + n * kb) return fail(MMS_ERR_INVALID_ARG, "input and output overlap%s");
   if (d_ws && ws_bytes < kStatusBytes) return fail(MMS_ERR_INVALID_ARG, "workspace too small%s");
   int* dev_err = d_ws ? static_cast<int*>(d_ws) : nullptr;
-  return check_launch(mms::launch_merge_pass((int)kb, false, d_in, d_out, (long long)n,
+  return check_launch(mms::launch_merge_pass((int)kb, mms::default_tile_warps((int)kb), false, d_in,
+                                             d_out, (long long)n,
                                              (long long)run_len, K,
                                              reinterpret_cast<const long long*>(d_table), dev_err,
                                              (cudaStream_t)stream), "merge_pass");

@@ -8,63 +8,84 @@
 //   1. stages the K segments into shared memory with 1-D TMA bulk copies
 //      (cp.async.bulk, one mbarrier; the < 16-byte ragged ends of each
 //      segment by plain loads), so every input byte is read from HBM once;
-//   2. merges them in ceil(log2 K) levels of pairwise block merges, each warp
-//      producing 1024-item output blocks with the conflict-free bitonic block
-//      merge (the paper merges 32+32 blocks in a minBlockHeap; the levels here
-//      play the heap's levels);
-//   3. writes the tile with coalesced 128-bit stores, so every output byte is
+//   2. merges them along a binary merge tree of ceil(log2 K) levels (the
+//      paper's minBlockHeap has the same levels).  Every tree node (a pair of
+//      sequences) is cut into 1024-item output blocks; warps take blocks from
+//      a shared counter in level order and wait only for the two child nodes
+//      of their block, not for whole levels.  A node's output is written into
+//      the span its segments were staged in, alternating between two buffers
+//      by level, so no block can overwrite data another block still reads.
+//      Each block is merged by the conflict-free warp bitonic block merge;
+//   3. writes the tile with one TMA bulk store, so every output byte is
 //      written once: 2 * S * sizeof(key) bytes of HBM traffic per tile.
 #include "mms_common.cuh"
 #include "mms_kernels.cuh"
 
 namespace mms {
 
-template <typename KeyT>
-struct MergeVec;
-template <>
-struct MergeVec<uint32_t> {
-  using T = uint4;
-  static constexpr int E = 4;
-};
-template <>
-struct MergeVec<uint64_t> {
-  using T = ulonglong2;
-  static constexpr int E = 2;
-};
-
-// Items of slack per segment in the staging buffer: the copied head before a
-// segment start (< E) and the rounding of its end (< E).
+// Shared-memory geometry of a merge CTA.  X: the staged segments, each at a
+// 16-byte aligned span start R_r (up to 2E-2 items of slack per segment), and
+// the even tree levels' outputs; Y: the odd levels' outputs (same spans).
 template <typename KeyT, int WARPS>
 struct MergeGeom {
-  static constexpr int E = MergeVec<KeyT>::E;
+  static constexpr int E = Vec16<KeyT>::E;
   static constexpr int S = WARPS * kBlockItems;
-  static constexpr int XCAP = S + kMaxFanout * 2 * E;   // staging buffer (also a level buffer)
-  static constexpr int YCAP = S;
-  static constexpr size_t bytes() {
-    return sizeof(KeyT) * ((size_t)XCAP + YCAP + (size_t)WARPS * kScratchItems);
-  }
+  static constexpr int CAP = S + kMaxFanout * 2 * E + E;
+  static constexpr size_t SCRATCH_OFF = sizeof(KeyT) * 2 * (size_t)CAP;
+  static constexpr size_t CTRL_OFF =
+      SCRATCH_OFF + sizeof(KeyT) * (size_t)WARPS * Scratch<KeyT>::ITEMS;
+  // control block: mbarrier (8), next item (4), error flag (4), done[32] (128)
+  static constexpr size_t BYTES = CTRL_OFF + 8 + 4 + 4 + 4 * 32;
 };
 
 size_t merge_pass_smem_bytes(int key_bytes, int warps) {
-  if (key_bytes == 4) return MergeGeom<uint32_t, kTileWarps32>::bytes();
-  return MergeGeom<uint64_t, kTileWarps64>::bytes();
-  (void)warps;
+  if (key_bytes == 4) {
+    switch (warps) {
+      case 4: return MergeGeom<uint32_t, 4>::BYTES;
+      case 8: return MergeGeom<uint32_t, 8>::BYTES;
+    }
+  } else {
+    switch (warps) {
+      case 2: return MergeGeom<uint64_t, 2>::BYTES;
+      case 4: return MergeGeom<uint64_t, 4>::BYTES;
+    }
+  }
+  return 0;
+}
+
+// Bounded wait until tree node `c` has all `nb` of its blocks written; gives
+// up after about two seconds, or at once when another warp has given up.
+__device__ __forceinline__ bool wait_node(const int* done, const int* err_flag, int c, int nb) {
+  if (c < 0) return true;
+  const volatile int* d = done;
+  const volatile int* ef = err_flag;
+  if (d[c] >= nb) return true;
+  const long long t0 = clock64();
+  for (long long it = 0; it < (1ll << 26); ++it) {
+    __nanosleep(32);
+    if (d[c] >= nb) return true;
+    if (*ef != 0 || clock64() - t0 > 4000000000ll) break;
+  }
+  return false;
 }
 
 template <typename KeyT, int WARPS, bool XOUT>
-__global__ void __launch_bounds__(WARPS * 32)
+__global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
     merge_pass_kernel(const KeyT* __restrict__ in, KeyT* __restrict__ out, long long n,
                       long long run_len, int K, const long long* __restrict__ table,
                       long long tpg, int* dev_err) {
   using G = MergeGeom<KeyT, WARPS>;
   constexpr int E = G::E;
   constexpr int S = G::S;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   KeyT* bufX = reinterpret_cast<KeyT*>(smem_raw);
-  KeyT* bufY = bufX + G::XCAP;
+  KeyT* bufY = bufX + G::CAP;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  KeyT* scr = bufY + G::YCAP + warp * kScratchItems;
+  KeyT* scr = reinterpret_cast<KeyT*>(smem_raw + G::SCRATCH_OFF) + warp * Scratch<KeyT>::ITEMS;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + G::CTRL_OFF);
+  int* next_item = reinterpret_cast<int*>(smem_raw + G::CTRL_OFF + 8);
+  int* err_flag = next_item + 1;
+  int* done = next_item + 2;
 
   const long long t = blockIdx.x;
   const long long g = t / tpg, j = t % tpg;
@@ -85,13 +106,14 @@ __global__ void __launch_bounds__(WARPS * 32)
   }
   // The pivot rows must describe segments inside their runs whose lengths sum
   // to this tile's size; anything else would overrun the staging buffer.
+  const long long want = (gsize - j * S) < S ? (gsize - j * S) : S;
   {
-    const long long want = (gsize - j * S) < S ? (gsize - j * S) : S;
     const bool bad_seg = act && (lo < 0 || hi < lo || hi > rlen);
     long long sum = act ? hi - lo : 0;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (__any_sync(0xffffffffu, bad_seg) || sum != want || K > kMaxFanout) {
+    if (__any_sync(0xffffffffu, bad_seg) || sum != want || K > kMaxFanout || K < 2 ||
+        (smem_u32addr(smem_raw) & 1023u) != 0) {
       if (threadIdx.x == 0) set_device_error(dev_err, kDevErrInternal);
       return;                                          // uniform over the CTA
     }
@@ -99,35 +121,46 @@ __global__ void __launch_bounds__(WARPS * 32)
   const long long gsrc = rstart + lo;                  // first item, global index
   const int len = act ? (int)(hi - lo) : 0;
   const int head = act ? (int)(gsrc % E) : 0;          // items copied before the segment
-  const int span = (head + len + E - 1) / E * E;       // staged extent, multiple of E
+  const int span = (head + len + E - 1) / E * E;       // staged span, multiple of E
   int incl = span;
+  int lincl = len;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int x = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += x;
+    const int y = __shfl_up_sync(0xffffffffu, lincl, o);
+    if (lane >= o) {
+      incl += x;
+      lincl += y;
+    }
   }
-  const int place = incl - span;                       // staged extent start (multiple of E)
-  const int my_off0 = place + head;
+  const int R = incl - span;                           // span start of segment `lane`
+  const int lpre = lincl - len;                        // items in segments before `lane`
   // Bulk part: [gsrc - head, floor_E(gsrc + len)); the rest by plain loads.
   const long long bulk_lo = gsrc - head;
   const long long bulk_hi = (gsrc + len) / E * E;
-  const unsigned bulk_bytes = (act && bulk_hi > bulk_lo) ? (unsigned)((bulk_hi - bulk_lo) * sizeof(KeyT)) : 0u;
+  const unsigned bulk_bytes =
+      (act && bulk_hi > bulk_lo) ? (unsigned)((bulk_hi - bulk_lo) * sizeof(KeyT)) : 0u;
 
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    *next_item = 0;
+    *err_flag = 0;
+  }
+  if (threadIdx.x < 32) done[threadIdx.x] = 0;
   __syncthreads();
   if (warp == 0) {
     unsigned total = bulk_bytes;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
-    if (lane == 0) mbar_arrive_expect_tx(&bar, total);
+    if (lane == 0) mbar_arrive_expect_tx(bar, total);
     __syncwarp();
-    if (bulk_bytes) bulk_g2s(bufX + place, in + bulk_lo, bulk_bytes, &bar);
+    if (bulk_bytes) bulk_g2s(bufX + R, in + bulk_lo, bulk_bytes, bar);
   } else if (warp == 1) {
     // Ragged ends, one segment at a time, consecutive lanes -> consecutive words.
     for (int r = 0; r < K; ++r) {
       const long long s_src = __shfl_sync(0xffffffffu, gsrc, r);
       const int s_len = __shfl_sync(0xffffffffu, len, r);
-      const int s_off = __shfl_sync(0xffffffffu, my_off0, r);
+      const int s_off = __shfl_sync(0xffffffffu, R + head, r);
       const long long s_bhi = __shfl_sync(0xffffffffu, bulk_hi, r);
       const long long s_blo = __shfl_sync(0xffffffffu, bulk_lo, r);
       const long long from = (s_bhi > s_blo) ? s_bhi : s_src;   // first item not bulk-copied
@@ -135,82 +168,159 @@ __global__ void __launch_bounds__(WARPS * 32)
       if (e < s_src + s_len) bufX[s_off + (int)(e - s_src)] = in[e];
     }
   }
-  const bool ok = mbar_wait_bounded(&bar, 0);
+
+  // Merge-tree nodes, one per lane, in level order: node (level l >= 1, pair q)
+  // merges child A = segments [q*2^l, q*2^l + 2^(l-1)) and child B = the rest
+  // of [q*2^l, (q+1)*2^l) (clipped to K).  Every warp derives the same table.
+  int nl = 0, nnodes = 0, c_level = 0, c_pair = 0, prev_start = 0, prev_count = 0;
+  {
+    int cnt = K, idx = 0, pidx = 0, pcnt = K;
+    for (int l = 1; cnt > 1; ++l) {
+      const int pairs = (cnt + 1) >> 1;
+      if (lane >= idx && lane < idx + pairs) {
+        c_level = l;
+        c_pair = lane - idx;
+        prev_start = pidx;                              // first node of level l-1
+        prev_count = pcnt;                              // sequences of level l-1
+      }
+      pidx = idx;
+      pcnt = pairs;
+      idx += pairs;
+      cnt = pairs;
+      nl = l;
+    }
+    nnodes = idx;
+  }
+  const bool is_node = lane < nnodes;
+  const int first = c_pair << c_level;                  // first segment of the node
+  const int mid = first + (1 << (c_level > 0 ? c_level - 1 : 0));
+  const int last = first + (1 << c_level);
+  auto seg_pre = [&](int s) {                           // items in segments [0, s)
+    const int ss = s < K ? s : K;
+    const int v = __shfl_sync(0xffffffffu, lpre, ss & 31);
+    return ss >= K ? (int)want : v;
+  };
+  const int pf = seg_pre(first), pm = seg_pre(mid), pl = seg_pre(last);
+  const int rf = __shfl_sync(0xffffffffu, R, first & 31);
+  const int hf = __shfl_sync(0xffffffffu, head, first & 31);
+  const int rm = __shfl_sync(0xffffffffu, R, mid & 31);
+  const int hm = __shfl_sync(0xffffffffu, head, mid & 31);
+  const int c_lenA = is_node ? pm - pf : 0;
+  const int c_lenB = is_node ? pl - pm : 0;
+  const int c_offA = (c_level == 1) ? rf + hf : rf;     // staged segment vs. child output
+  const int c_offB = (mid < K) ? ((c_level == 1) ? rm + hm : rm) : 0;
+  const int c_out = rf;
+  const int c_nb = (c_lenA + c_lenB + kBlockItems - 1) / kBlockItems;
+  int c_first = c_nb;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int x = __shfl_up_sync(0xffffffffu, c_first, o);
+    if (lane >= o) c_first += x;
+  }
+  const int total_items = __shfl_sync(0xffffffffu, c_first, (nnodes - 1) & 31);
+  c_first -= c_nb;
+  const int c_depA = (c_level >= 2) ? prev_start + 2 * c_pair : -1;
+  const int c_depB =
+      (c_level >= 2 && 2 * c_pair + 1 < prev_count) ? prev_start + 2 * c_pair + 1 : -1;
+
+  const bool ok = mbar_wait_bounded(bar, 0);
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) set_device_error(dev_err, kDevErrTimeout);
     return;
   }
 
-  // ceil(log2 K) merge levels between the two buffers.
-  int my_off = my_off0, my_len = len;
-  int nseq = K;
-  KeyT* src = bufX;
-  KeyT* dst = bufY;
-  while (nseq > 1) {
-    cta_merge_level(src, dst, my_off, my_len, nseq, scr, warp, WARPS, lane);
-    next_seq(my_off, my_len, nseq, lane);
-    nseq = (nseq + 1) >> 1;
-    __syncthreads();
-    KeyT* tmp = src;
-    src = dst;
-    dst = tmp;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(next_item, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total_items) break;
+    const unsigned sel = __ballot_sync(0xffffffffu, is_node && c_first <= item && c_nb > 0);
+    const int c = 31 - __clz(sel);
+    const int level = __shfl_sync(0xffffffffu, c_level, c);
+    const int lenA = __shfl_sync(0xffffffffu, c_lenA, c);
+    const int lenB = __shfl_sync(0xffffffffu, c_lenB, c);
+    const int offA = __shfl_sync(0xffffffffu, c_offA, c);
+    const int offB = __shfl_sync(0xffffffffu, c_offB, c);
+    const int outo = __shfl_sync(0xffffffffu, c_out, c);
+    const int fi = __shfl_sync(0xffffffffu, c_first, c);
+    const int depA = __shfl_sync(0xffffffffu, c_depA, c);
+    const int depB = __shfl_sync(0xffffffffu, c_depB, c);
+    const int nbA = __shfl_sync(0xffffffffu, c_nb, depA & 31);
+    const int nbB = __shfl_sync(0xffffffffu, c_nb, depB & 31);
+    int ready = 1;
+    if (lane == 0)
+      ready = wait_node(done, err_flag, depA, nbA) && wait_node(done, err_flag, depB, nbB);
+    ready = __shfl_sync(0xffffffffu, ready, 0);
+    if (!ready) {
+      if (lane == 0) atomicExch(err_flag, 1);
+      continue;
+    }
+    __threadfence_block();
+    const KeyT* src = (level & 1) ? bufX : bufY;        // level l reads level l-1's buffer
+    KeyT* dst = (level & 1) ? bufY : bufX;
+    const KeyT* A = src + offA;
+    const KeyT* B = src + offB;
+    const int L = lenA + lenB;
+    const int d0 = (item - fi) * kBlockItems;
+    const int m = (L - d0) < kBlockItems ? (L - d0) : kBlockItems;
+    const int a0 = warp_corank(A, lenA, B, lenB, d0, lane);
+    const int a1 = (d0 + m == L) ? lenA : warp_corank(A, lenA, B, lenB, d0 + m, lane);
+    const int X = a1 - a0;
+    warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, scr, lane,
+                           XOUT && level == nl);
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      atomicAdd(&done[c], 1);
+    }
   }
-  // src now holds the tile at offset my_off of lane 0 (0 when K > 1).
-  const int m = __shfl_sync(0xffffffffu, my_len, 0);
-  const KeyT* res = src + __shfl_sync(0xffffffffu, my_off, 0);
+  __syncthreads();
+  if (*err_flag) {
+    if (threadIdx.x == 0) set_device_error(dev_err, kDevErrTimeout);
+    return;
+  }
+  // The root node's output is the tile, at span start 0 of the last level's buffer.
+  const KeyT* res = (nl & 1) ? bufY : bufX;
+  const int m = (int)want;
   KeyT* dstg = out + gstart + j * S;
-  using V = typename MergeVec<KeyT>::T;
-  const int nv = m / E;
-  if (((size_t)res & 15) == 0) {
-    const V* s4 = reinterpret_cast<const V*>(res);
-    V* d4 = reinterpret_cast<V*>(dstg);
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-      V x = s4[i];
-      if constexpr (XOUT) {
-        uint32_t* w = reinterpret_cast<uint32_t*>(&x);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) w[c] = ordered_to_f32(w[c]);
-      }
-      d4[i] = x;
-    }
-  } else {
-    for (int i = threadIdx.x; i < nv * E; i += blockDim.x) {
-      KeyT x = res[i];
-      if constexpr (XOUT) x = (KeyT)ordered_to_f32((uint32_t)x);
-      dstg[i] = x;
-    }
-  }
-  for (int i = nv * E + (int)threadIdx.x; i < m; i += blockDim.x) {
-    KeyT x = res[i];
-    if constexpr (XOUT) x = (KeyT)ordered_to_f32((uint32_t)x);
-    dstg[i] = x;
-  }
+  const int body = m / E * E;
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0 && body > 0) bulk_s2g_and_wait(dstg, res, (unsigned)(body * sizeof(KeyT)));
+  for (int i = body + (int)threadIdx.x; i < m; i += blockDim.x) dstg[i] = res[i];
 }
 
 template <typename KeyT, int WARPS, bool XOUT>
 static cudaError_t launch_merge_t(const void* in, void* out, long long n, long long run_len, int K,
                                   const long long* table, int* dev_err, cudaStream_t s) {
-  const size_t smem = MergeGeom<KeyT, WARPS>::bytes();
+  const size_t smem = MergeGeom<KeyT, WARPS>::BYTES;
   auto k = merge_pass_kernel<KeyT, WARPS, XOUT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long ntiles = num_tiles(sizeof(KeyT), n, run_len, K);
-  const long long tpg = tiles_per_group(sizeof(KeyT), run_len, K);
+  const long long S = (long long)WARPS * kBlockItems;
+  const long long ntiles = num_tiles(S, n, run_len, K);
+  const long long tpg = run_len * K / S;
   k<<<(unsigned)ntiles, WARPS * 32, smem, s>>>(static_cast<const KeyT*>(in), static_cast<KeyT*>(out),
                                               n, run_len, K, table, tpg, dev_err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_merge_pass(int key_bytes, bool xout, const void* in, void* out, long long n,
-                              long long run_len, int K, const long long* table, int* dev_err,
-                              cudaStream_t s) {
+cudaError_t launch_merge_pass(int key_bytes, int tile_warps, bool xout, const void* in, void* out,
+                              long long n, long long run_len, int K, const long long* table,
+                              int* dev_err, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (key_bytes == 4) {
-    if (xout)
-      return launch_merge_t<uint32_t, kTileWarps32, true>(in, out, n, run_len, K, table, dev_err, s);
-    return launch_merge_t<uint32_t, kTileWarps32, false>(in, out, n, run_len, K, table, dev_err, s);
+    if (tile_warps == 8)
+      return xout ? launch_merge_t<uint32_t, 8, true>(in, out, n, run_len, K, table, dev_err, s)
+                  : launch_merge_t<uint32_t, 8, false>(in, out, n, run_len, K, table, dev_err, s);
+    if (tile_warps == 4)
+      return xout ? launch_merge_t<uint32_t, 4, true>(in, out, n, run_len, K, table, dev_err, s)
+                  : launch_merge_t<uint32_t, 4, false>(in, out, n, run_len, K, table, dev_err, s);
+    return cudaErrorInvalidValue;
   }
-  return launch_merge_t<uint64_t, kTileWarps64, false>(in, out, n, run_len, K, table, dev_err, s);
+  if (tile_warps == 4) return launch_merge_t<uint64_t, 4, false>(in, out, n, run_len, K, table, dev_err, s);
+  if (tile_warps == 2) return launch_merge_t<uint64_t, 2, false>(in, out, n, run_len, K, table, dev_err, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace mms

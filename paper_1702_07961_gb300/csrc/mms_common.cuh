@@ -4,10 +4,11 @@
 // warp co-rank (merge-path) search in shared memory, and TMA/mbarrier PTX.
 //
 // Shared-memory discipline (Sec. 3.2 and Sec. 5.2): every shared-memory access
-// a warp makes is either 32 consecutive items (any base: one bank each), a
-// fixed permutation of banks inside 32-word windows (padded rows, XOR
-// swizzle), or a probe at an odd stride -- never a data-dependent gather -- so
-// no input can cause a bank conflict.
+// a warp makes is 32 consecutive items (any base: one bank each), a row of a
+// padded table read with 16-byte vectors whose rows start 4 banks apart, a
+// 16-byte chunk whose position is XOR-permuted by the lane id, or a probe at an
+// odd stride -- never a data-dependent gather -- so no input can cause a bank
+// conflict.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,8 +20,6 @@ namespace mms {
 
 constexpr int kWarpSize = 32;
 constexpr int kBlockItems = 1024;       // one warp block: 32 lanes x 32 registers
-constexpr int kScratchRow = 33;         // padded row of the per-warp transpose scratch
-constexpr int kScratchItems = 32 * kScratchRow;
 
 // ---------------------------------------------------------------------------
 // Keys.  KeyT is uint32_t (u32 keys, and f32 keys after the transform) or
@@ -40,6 +39,38 @@ __device__ __forceinline__ uint32_t ordered_to_f32(uint32_t y) {
   return y ^ ((uint32_t)((int32_t)~y >> 31) | 0x80000000u);
 }
 
+// 16-byte vectors of keys.
+template <typename KeyT>
+struct Vec16;
+template <>
+struct Vec16<uint32_t> {
+  using T = uint4;
+  static constexpr int E = 4;
+  __device__ static void unpack(const uint4& x, uint32_t* o) {
+    o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+  }
+  __device__ static uint4 pack(const uint32_t* o) { return make_uint4(o[0], o[1], o[2], o[3]); }
+};
+template <>
+struct Vec16<uint64_t> {
+  using T = ulonglong2;
+  static constexpr int E = 2;
+  __device__ static void unpack(const ulonglong2& x, uint64_t* o) {
+    o[0] = x.x; o[1] = x.y;
+  }
+  __device__ static ulonglong2 pack(const uint64_t* o) { return make_ulonglong2(o[0], o[1]); }
+};
+
+// Per-warp transpose scratch: 32 rows, each padded so that consecutive rows
+// start 4 banks apart (u32: 36 words; u64: 34 items = 68 words), which makes
+// both the row-wise 16-byte vector reads and the column-wise scalar writes
+// conflict-free.
+template <typename KeyT>
+struct Scratch {
+  static constexpr int ROW = sizeof(KeyT) == 4 ? 36 : 34;
+  static constexpr int ITEMS = 32 * ROW;
+};
+
 template <typename KeyT>
 __device__ __forceinline__ void cas(KeyT& a, KeyT& b) {
   const KeyT lo = a < b ? a : b;
@@ -49,9 +80,9 @@ __device__ __forceinline__ void cas(KeyT& a, KeyT& b) {
 }
 
 // Compare-exchange whose direction is chosen per lane: with flip set the
-// larger key goes to a.  Flipping every stage of a bitonic merge whose stride
-// bit is set in the lane id leaves the lane's sorted items XOR-permuted by the
-// lane id, which makes the following shared-memory store conflict-free.
+// larger key goes to a.  Flipping the stages of a bitonic merge whose stride
+// bit is set in a lane mask leaves the lane's sorted items XOR-permuted by
+// that mask, which makes the following shared-memory store conflict-free.
 template <typename KeyT>
 __device__ __forceinline__ void cas_dir(KeyT& a, KeyT& b, bool flip) {
   const KeyT lo = a < b ? a : b;
@@ -66,9 +97,7 @@ __device__ __forceinline__ KeyT shfl_xor(KeyT v, int mask) {
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory loads that the compiler may not merge: the two halves of a
-// register that straddles the A/B boundary are fetched by two instructions,
-// each with its own lanes active, so neither can conflict.
+// Shared-memory accesses the compiler may not merge or reorder across.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -101,25 +130,16 @@ __device__ __forceinline__ int warp_corank(const KeyT* A, int lenA, const KeyT* 
   int lo = d - lenB > 0 ? d - lenB : 0;
   int hi = d < lenA ? d : lenA;
   while (hi > lo) {
-    const int range = hi - lo;
-    const int step = ((range + 31) >> 5) | 1;
+    const int step = ((hi - lo + 31) >> 5) | 1;
     const int i = lo + lane * step;
     bool p = true;                                 // positions >= hi count as "true"
     if (i < hi) p = A[i] > B[d - 1 - i];           // A[i] comes after B[d-1-i]
     const unsigned bal = __ballot_sync(0xffffffffu, p);
-    if (bal == 0u) {
-      lo = lo + 31 * step + 1;
-    } else {
-      const int f = __ffs(bal) - 1;
-      if (f == 0) {
-        hi = lo;
-      } else {
-        const int nlo = lo + (f - 1) * step + 1;
-        const int top = lo + f * step;
-        hi = top < hi ? top : hi;
-        lo = nlo;
-      }
-    }
+    const int f = __ffs(bal) - 1;                  // first "true" probe, -1 if none
+    const int top = lo + f * step;
+    const int nlo = (f <= 0) ? (f == 0 ? lo : lo + 31 * step + 1) : top - step + 1;
+    hi = (f < 0) ? hi : (top < hi ? top : hi);
+    lo = nlo;
   }
   return lo;
 }
@@ -133,37 +153,46 @@ __device__ __forceinline__ int warp_corank(const KeyT* A, int lenA, const KeyT* 
 // into out[0, m) ascending.  The warp reads C = A ascending ++ pads ++ B
 // descending -- a bitonic sequence -- in the striped layout (item 32k+lane in
 // register k: 32 consecutive words per load), runs the five half-cleaners of
-// stride >= 32 inside registers, transposes through a padded scratch to the
+// stride >= 32 inside registers, transposes through the padded scratch to the
 // blocked layout (items 32*lane .. 32*lane+31 in one lane), runs the five
-// half-cleaners of stride < 32 inside registers with lane-flipped directions,
-// and stores item 32*lane + (j ^ lane) from register j: every shared-memory
-// access of the warp touches 32 distinct banks (16 per half-warp for 64-bit
-// keys), whatever the data.
+// half-cleaners of stride < 32 inside registers, flipping the direction of the
+// strides of 16 bytes and more by lane bits, and stores 16-byte chunks whose
+// position in the row is XOR-permuted by the lane: every shared-memory access
+// of the warp is conflict-free whatever the data.
 // ---------------------------------------------------------------------------
+
+// Register k of lane l receives C[32k + l]: A[32k + l] when that is below X,
+// B[1023 - 32k - l] when it is at or above 1024 - Y, a pad in between.  The A
+// and B halves of a register are fetched by two predicated loads, so each
+// load instruction touches consecutive words only.
 template <typename KeyT>
 __device__ __forceinline__ void warp_load_bitonic(const KeyT* A, int X, const KeyT* B, int Y,
                                                   KeyT (&v)[32], int lane) {
-  const int kA = X >> 5;                    // registers [0, kA) come from A only
-  const int kB = (kBlockItems - Y + 31) >> 5;  // registers [kB, 32) come from B only
-  const KeyT* Bend = B + (kBlockItems - 1);    // C[i] = B[1023 - i] for i >= 1024 - Y
+  const KeyT* pa = A + lane;                         // C[32k+lane] = A[32k+lane]
+  const KeyT* pb = B + (kBlockItems - 1 - lane);     // C[32k+lane] = B[1023-32k-lane]
+  const int xa = X - lane;                           // 32k + lane < X  <=>  32k < xa
+  const int xb = kBlockItems - Y - lane;             // 32k + lane >= 1024 - Y  <=>  32k >= xb
 #pragma unroll
   for (int k = 0; k < 32; ++k) {
-    const int i = 32 * k + lane;
-    if (k < kA) {
-      v[k] = A[i];
-    } else if (k >= kB) {
-      v[k] = Bend[-i];
-    } else {
-      KeyT t = key_pad<KeyT>();
-      lds_pred(t, A + i, i < X);
-      lds_pred(t, Bend - i, i >= kBlockItems - Y);
-      v[k] = t;
-    }
+    KeyT t = key_pad<KeyT>();
+    lds_pred(t, pa + 32 * k, 32 * k < xa);
+    lds_pred(t, pb - 32 * k, 32 * k >= xb);
+    v[k] = t;
   }
+}
+
+// Flip mask of a lane: the in-row XOR that makes its 16-byte chunk stores hit
+// distinct banks within each quarter-warp (a multiple of the chunk size).
+template <typename KeyT>
+__device__ __forceinline__ int flip_mask(int lane) {
+  constexpr int E = Vec16<KeyT>::E;
+  return (lane & (32 / E - 1)) * E;
 }
 
 template <typename KeyT>
 __device__ __forceinline__ void warp_bitonic_1024(KeyT (&v)[32], KeyT* scr, int lane) {
+  using V = Vec16<KeyT>;
+  constexpr int ROW = Scratch<KeyT>::ROW;
   // half-cleaners of stride 512 .. 32: register distance 16 .. 1
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) {
@@ -171,58 +200,112 @@ __device__ __forceinline__ void warp_bitonic_1024(KeyT (&v)[32], KeyT* scr, int 
     for (int k = 0; k < 32; ++k)
       if ((k & s) == 0) cas(v[k], v[k + s]);
   }
-  // striped -> blocked through the padded scratch (row k holds items 32k..32k+31)
+  // striped -> blocked: row k of the scratch holds items 32k .. 32k+31
 #pragma unroll
-  for (int k = 0; k < 32; ++k) scr[kScratchRow * k + lane] = v[k];
+  for (int k = 0; k < 32; ++k) scr[ROW * k + lane] = v[k];
   __syncwarp();
+  const typename V::T* row = reinterpret_cast<const typename V::T*>(scr + ROW * lane);
 #pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = scr[kScratchRow * lane + j];
+  for (int c = 0; c < 32 / V::E; ++c) V::unpack(row[c], &v[c * V::E]);
   __syncwarp();
-  // half-cleaners of stride 16 .. 1 inside the lane, direction flipped by lane bit
+  // half-cleaners of stride 16 .. 1 inside the lane
+  const int F = flip_mask<KeyT>(lane);
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) {
-    const bool f = (lane & s) != 0;
+    const bool f = (F & s) != 0;
 #pragma unroll
     for (int k = 0; k < 32; ++k)
       if ((k & s) == 0) cas_dir(v[k], v[k + s], f);
   }
 }
 
-// Stores the lane-XOR-permuted sorted block: register j holds item 32*lane + (j ^ lane).
+__device__ __forceinline__ void sts_addr(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void sts_addr(uint32_t addr, uint64_t v) {
+  asm volatile("st.shared.b64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+__device__ __forceinline__ void sts128(uint32_t addr, const uint32_t* v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v[0]), "r"(v[1]),
+               "r"(v[2]), "r"(v[3])
+               : "memory");
+}
+__device__ __forceinline__ void sts128(uint32_t addr, const uint64_t* v) {
+  asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(addr), "l"(v[0]), "l"(v[1]) : "memory");
+}
+
+__device__ __forceinline__ void sts128_pred(uint32_t addr, const uint32_t* v, bool p) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t@q st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n\t}\n" ::"r"(
+          addr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"((int)p)
+      : "memory");
+}
+__device__ __forceinline__ void sts128_pred(uint32_t addr, const uint64_t* v, bool p) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t@q st.shared.v2.b64 [%0], {%1, %2};\n\t}\n" ::"r"(
+          addr),
+      "l"(v[0]), "l"(v[1]), "r"((int)p)
+      : "memory");
+}
+
+// Stores the sorted block: register j of the lane holds item 32*lane + (j ^ F),
+// F = flip_mask(lane).  `out` must be 16-byte aligned.  Items go out in 16-byte
+// chunks (chunk c of the lane lands at chunk c ^ (F / E) of its row); for a
+// short block the chunks wholly below m are stored this way and the one chunk
+// that straddles m item by item (by a single lane).  `xout` undoes the float
+// transform on the way out.
 template <typename KeyT>
-__device__ __forceinline__ void warp_store_block(KeyT* out, int m, const KeyT (&v)[32], int lane) {
-  KeyT* base = out + 32 * lane;
-  if (m == kBlockItems) {
+__device__ __forceinline__ void warp_store_block(KeyT* out, int m, KeyT (&v)[32], int lane,
+                                                 bool xout) {
+  constexpr int E = Vec16<KeyT>::E;
+  constexpr int SZ = (int)sizeof(KeyT);
+  if (xout) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) base[j ^ lane] = v[j];
-  } else {
+    for (int j = 0; j < 32; ++j) v[j] = (KeyT)ordered_to_f32((uint32_t)v[j]);
+  }
+  const int F = flip_mask<KeyT>(lane);
+  const uint32_t row = smem_u32addr(out + 32 * lane);
+  const int room = m - 32 * lane;                    // items of this row below m
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int e = 32 * lane + (j ^ lane);
-      if (e < m) base[j ^ lane] = v[j];
+  for (int c = 0; c < 32 / E; ++c) {
+    const int pos = (c * E) ^ F;                      // item offset of the chunk in the row
+    sts128_pred(row + (uint32_t)(pos * SZ), &v[c * E], pos + E <= room);
+  }
+  if (m < kBlockItems && (m % E) != 0) {
+#pragma unroll
+    for (int c = 0; c < 32 / E; ++c) {
+      const int pos = (c * E) ^ F;
+#pragma unroll
+      for (int w = 0; w < E; ++w)
+        if (pos < room && pos + E > room && pos + w < room)
+          sts_addr(row + (uint32_t)((pos + w) * SZ), v[c * E + w]);
     }
   }
 }
 
 template <typename KeyT>
 __device__ __forceinline__ void warp_merge_block(const KeyT* A, int X, const KeyT* B, int Y,
-                                                 KeyT* out, KeyT* scr, int lane) {
+                                                 KeyT* out, KeyT* scr, int lane, bool xout) {
   KeyT v[32];
   warp_load_bitonic(A, X, B, Y, v, lane);
   warp_bitonic_1024(v, scr, lane);
-  warp_store_block(out, X + Y, v, lane);
+  warp_store_block<KeyT>(out, X + Y, v, lane, xout);
 }
 
 // ---------------------------------------------------------------------------
-// One CTA merge level.  Sequence q (q < 32) of `src` is described by lane q's
-// (off, len); sequences (2p, 2p+1) are merged into `dst`, packed in pair
-// order.  Work items are the 1024-item output blocks of every pair, dealt to
-// the warps round-robin.  next_seq() gives the descriptors of the outputs.
+// One CTA merge level with a barrier after it (used by the base case, whose
+// blocks are all full).  Sequence q (q < 32) of `src` is described by lane
+// q's (off, len); sequences (2p, 2p+1) are merged into `dst`, pair outputs
+// packed in pair order, 16-byte aligned.  Work items are the 1024-item output
+// blocks of every pair, dealt to the warps round-robin.  next_seq() gives the
+// descriptors of the outputs.
 // ---------------------------------------------------------------------------
 template <typename KeyT>
 __device__ __forceinline__ void cta_merge_level(const KeyT* src, KeyT* dst, int my_off, int my_len,
                                                 int nseq, KeyT* scr, int warp, int nwarps,
-                                                int lane) {
+                                                int lane, bool xout) {
+  constexpr int E = Vec16<KeyT>::E;
   int item = 0;
   int outoff = 0;
   for (int q = 0; 2 * q < nseq; ++q) {
@@ -237,27 +320,30 @@ __device__ __forceinline__ void cta_merge_level(const KeyT* src, KeyT* dst, int 
       if (item % nwarps != warp) continue;
       const int m = (L - d0) < kBlockItems ? (L - d0) : kBlockItems;
       const int a0 = warp_corank(A, a_len, B, b_len, d0, lane);
-      const int a1 = warp_corank(A, a_len, B, b_len, d0 + m, lane);
+      const int a1 = (d0 + m == L) ? a_len : warp_corank(A, a_len, B, b_len, d0 + m, lane);
       const int X = a1 - a0;
-      warp_merge_block(A + a0, X, B + (d0 - a0), m - X, dst + outoff + d0, scr, lane);
+      warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outoff + d0, scr, lane, xout);
     }
-    outoff += L;
+    outoff += (L + E - 1) / E * E;
   }
 }
 
 // Descriptors of the pair outputs of a level: lane p gets (packed offset, length).
+template <typename KeyT>
 __device__ __forceinline__ void next_seq(int& my_off, int& my_len, int nseq, int lane) {
+  constexpr int E = Vec16<KeyT>::E;
   const int l0 = __shfl_sync(0xffffffffu, my_len, (2 * lane) & 31);
   const int l1 = __shfl_sync(0xffffffffu, my_len, (2 * lane + 1) & 31);
   int len = 0;
   if (2 * lane < nseq) len = l0 + ((2 * lane + 1 < nseq) ? l1 : 0);
-  int incl = len;
+  const int span = (len + E - 1) / E * E;
+  int incl = span;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int t = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += t;
   }
-  my_off = incl - len;
+  my_off = incl - span;
   my_len = len;
 }
 
@@ -304,6 +390,22 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
           smem_u32addr(dst_smem)),
       "l"(src_gmem), "r"(bytes), "r"(smem_u32addr(bar))
       : "memory");
+}
+
+// Makes this thread's generic-proxy shared-memory writes visible to TMA.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bulk copy of `bytes` (multiple of 16, 16-byte aligned) from this CTA's
+// shared memory to global memory; waits until the copy has completed.
+__device__ __forceinline__ void bulk_s2g_and_wait(void* dst_gmem, const void* src_smem,
+                                                  unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
+               "r"(smem_u32addr(src_smem)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 __device__ __forceinline__ void set_device_error(int* err, int code) {

@@ -179,12 +179,11 @@ __global__ void __launch_bounds__(128)
   if (act) table[t * K + lane] = d;
 }
 
-cudaError_t launch_splitter(int key_bytes, const void* in, long long n, long long run_len, int K,
-                            long long* table, cudaStream_t s) {
-  const long long S = tile_items(key_bytes);
-  const long long ntiles = num_tiles(key_bytes, n, run_len, K);
+cudaError_t launch_splitter(int key_bytes, long long S, const void* in, long long n,
+                            long long run_len, int K, long long* table, cudaStream_t s) {
+  const long long ntiles = num_tiles(S, n, run_len, K);
   if (ntiles <= 0) return cudaSuccess;
-  const long long tpg = tiles_per_group(key_bytes, run_len, K);
+  const long long tpg = run_len * K / S;
   const unsigned grid = (unsigned)((ntiles + 3) / 4);
   if (key_bytes == 4)
     splitter_kernel<uint32_t><<<grid, 128, 0, s>>>(static_cast<const uint32_t*>(in), n, run_len, K,

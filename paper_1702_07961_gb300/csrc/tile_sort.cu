@@ -36,7 +36,8 @@ __device__ __forceinline__ void lane_sort32(KeyT (&v)[32]) {
 }
 
 // Sorts 1024 keys held as 32 per lane (any assignment) into the blocked
-// layout: after the call register j of lane l holds sorted item 32*l + (j ^ l).
+// layout: after the call register j of lane l holds sorted item
+// 32*l + (j ^ flip_mask(l)), the layout warp_store_block writes out.
 // Level lg merges runs of 2^(lg-1) lanes: a reversed-partner stage across the
 // run pair, lane half-cleaners by shuffle, then in-lane half-cleaners.
 template <typename KeyT>
@@ -65,35 +66,13 @@ __device__ __forceinline__ void warp_sort_1024(KeyT (&v)[32], int lane) {
     }
 #pragma unroll
     for (int s = 16; s >= 1; s >>= 1) {
-      const bool f = (lg == 5) && ((lane & s) != 0);
+      const bool f = (lg == 5) && ((flip_mask<KeyT>(lane) & s) != 0);
 #pragma unroll
       for (int k = 0; k < 32; ++k)
         if ((k & s) == 0) cas_dir(v[k], v[k + s], f);
     }
   }
 }
-
-// Vector of 16 bytes.
-template <typename KeyT>
-struct Vec16;
-template <>
-struct Vec16<uint32_t> {
-  using T = uint4;
-  static constexpr int E = 4;
-  __device__ static void unpack(const uint4& x, uint32_t* o) {
-    o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
-  }
-  __device__ static uint4 pack(const uint32_t* o) { return make_uint4(o[0], o[1], o[2], o[3]); }
-};
-template <>
-struct Vec16<uint64_t> {
-  using T = ulonglong2;
-  static constexpr int E = 2;
-  __device__ static void unpack(const ulonglong2& x, uint64_t* o) {
-    o[0] = x.x; o[1] = x.y;
-  }
-  __device__ static ulonglong2 pack(const uint64_t* o) { return make_ulonglong2(o[0], o[1]); }
-};
 
 template <typename KeyT, bool XIN>
 __device__ __forceinline__ KeyT xform_in(KeyT k) {
@@ -106,37 +85,28 @@ __device__ __forceinline__ KeyT xform_out(KeyT k) {
   return k;
 }
 
-// Coalesced 128-bit copy of `m` items from shared memory to global memory.
-template <typename KeyT, bool XOUT>
-__device__ __forceinline__ void cta_store_out(const KeyT* src, KeyT* dst, int m) {
-  using V = Vec16<KeyT>;
-  const int nv = m / V::E;
-  const typename V::T* s4 = reinterpret_cast<const typename V::T*>(src);
-  typename V::T* d4 = reinterpret_cast<typename V::T*>(dst);
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-    typename V::T x = s4[i];
-    if constexpr (XOUT) {
-      KeyT t[V::E];
-      V::unpack(x, t);
-#pragma unroll
-      for (int c = 0; c < V::E; ++c) t[c] = xform_out<KeyT, XOUT>(t[c]);
-      x = V::pack(t);
-    }
-    d4[i] = x;
-  }
-  for (int i = nv * V::E + (int)threadIdx.x; i < m; i += blockDim.x)
-    dst[i] = xform_out<KeyT, XOUT>(src[i]);
+// Writes the sorted tile src[0, m) to global memory: one TMA bulk store of the
+// 16-byte-aligned body, plain stores for the < 16-byte tail.  Every thread
+// must call it (it contains a barrier).
+template <typename KeyT>
+__device__ __forceinline__ void cta_store_tile(const KeyT* src, KeyT* dst, int m) {
+  constexpr int E = 16 / sizeof(KeyT);
+  const int body = m / E * E;
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0 && body > 0) bulk_s2g_and_wait(dst, src, (unsigned)(body * sizeof(KeyT)));
+  for (int i = body + (int)threadIdx.x; i < m; i += blockDim.x) dst[i] = src[i];
 }
 
 template <typename KeyT, int WARPS, bool XIN, bool XOUT>
-__global__ void __launch_bounds__(WARPS * 32)
+__global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
     tile_sort_kernel(const KeyT* __restrict__ in, KeyT* out, long long n) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   constexpr int T = WARPS * kBlockItems;
   KeyT* bufX = reinterpret_cast<KeyT*>(smem_raw);
   KeyT* bufY = bufX + T;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  KeyT* scr = bufY + T + warp * kScratchItems;
+  KeyT* scr = bufY + T + warp * Scratch<KeyT>::ITEMS;
 
   const long long base = (long long)blockIdx.x * T;
   const long long wbase = base + (long long)warp * kBlockItems;
@@ -168,7 +138,14 @@ __global__ void __launch_bounds__(WARPS * 32)
   }
 
   warp_sort_1024(v, lane);
-  warp_store_block(bufX + warp * kBlockItems, kBlockItems, v, lane);
+  const long long trem = n - base;
+  const int m = trem >= T ? T : (int)trem;
+  if constexpr (WARPS == 1) {
+    warp_store_block<KeyT>(bufX, kBlockItems, v, lane, XOUT);
+    cta_store_tile(bufX, out + base, m);
+    return;
+  }
+  warp_store_block<KeyT>(bufX + warp * kBlockItems, kBlockItems, v, lane, false);
   __syncthreads();
 
   // CTA levels: merge the warps' sorted blocks pairwise up to the tile.
@@ -182,21 +159,21 @@ __global__ void __launch_bounds__(WARPS * 32)
   KeyT* dst = bufY;
   int nseq = WARPS;
   while (nseq > 1) {
-    cta_merge_level(src, dst, my_off, my_len, nseq, scr, warp, WARPS, lane);
-    next_seq(my_off, my_len, nseq, lane);
+    cta_merge_level<KeyT>(src, dst, my_off, my_len, nseq, scr, warp, WARPS, lane,
+                          XOUT && nseq <= 2);
+    next_seq<KeyT>(my_off, my_len, nseq, lane);
     nseq = (nseq + 1) >> 1;
     __syncthreads();
     KeyT* t = src;
     src = dst;
     dst = t;
   }
-  const long long trem = n - base;
-  const int m = trem >= T ? T : (int)trem;
-  cta_store_out<KeyT, XOUT>(src, out + base, m);
+  cta_store_tile(src, out + base, m);
 }
 
 size_t tile_sort_smem_bytes(int key_bytes, int warps) {
-  return (size_t)key_bytes * (2 * warps * kBlockItems + warps * kScratchItems);
+  const size_t scratch = key_bytes == 8 ? Scratch<uint64_t>::ITEMS : Scratch<uint32_t>::ITEMS;
+  return (size_t)key_bytes * (2 * warps * kBlockItems + warps * scratch);
 }
 
 template <typename KeyT, int WARPS, bool XIN, bool XOUT>
@@ -211,15 +188,26 @@ static cudaError_t launch_tile_sort_t(const void* in, void* out, long long n, cu
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_sort(int key_bytes, bool xin, bool xout, const void* in, void* out,
-                             long long n, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
+template <int WARPS>
+static cudaError_t launch_tile_sort_w(int key_bytes, bool xin, bool xout, const void* in, void* out,
+                                      long long n, cudaStream_t s) {
   if (key_bytes == 4) {
-    if (xin && xout) return launch_tile_sort_t<uint32_t, kTileWarps32, true, true>(in, out, n, s);
-    if (xin) return launch_tile_sort_t<uint32_t, kTileWarps32, true, false>(in, out, n, s);
-    return launch_tile_sort_t<uint32_t, kTileWarps32, false, false>(in, out, n, s);
+    if (xin && xout) return launch_tile_sort_t<uint32_t, WARPS, true, true>(in, out, n, s);
+    if (xin) return launch_tile_sort_t<uint32_t, WARPS, true, false>(in, out, n, s);
+    return launch_tile_sort_t<uint32_t, WARPS, false, false>(in, out, n, s);
   }
-  return launch_tile_sort_t<uint64_t, kTileWarps64, false, false>(in, out, n, s);
+  return launch_tile_sort_t<uint64_t, WARPS, false, false>(in, out, n, s);
+}
+
+cudaError_t launch_tile_sort(int key_bytes, int tile_warps, bool xin, bool xout, const void* in,
+                             void* out, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  switch (tile_warps) {
+    case 2: return launch_tile_sort_w<2>(key_bytes, xin, xout, in, out, n, s);
+    case 4: return launch_tile_sort_w<4>(key_bytes, xin, xout, in, out, n, s);
+    case 8: return launch_tile_sort_w<8>(key_bytes, xin, xout, in, out, n, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace mms

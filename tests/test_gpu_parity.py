@@ -278,3 +278,20 @@ def test_full_size_interleaved_2p28(gpu, dtype):
         assert torch.equal(t, want)
     else:
         assert torch.equal(t.to(torch.int64) & 0xFFFFFFFF, iota)
+
+
+@pytest.mark.parametrize("dtype,tile", [(np.uint32, 4096), (np.uint64, 2048), (np.float32, 4096)])
+@pytest.mark.parametrize("fanout", [0, 2, 5, 8])
+def test_sort_other_tile_width(gpu, dtype, tile, fanout):
+    n = tile * 37 + 123
+    keys = synth.normal_f32(n, 3) if np.dtype(dtype) == np.float32 else synth.uniform(n, 4, dtype) % dtype(1000)
+    want, _ = oracle.sort(keys)
+    t = to_dev(keys)
+    gpu.sort_keys(t, fanout=fanout, kt=kt_of(dtype, gpu), tile_items=tile)
+    assert_bits_equal(to_host(t, keys.dtype), want)
+
+
+def test_bad_tile_width_is_rejected(gpu):
+    t = to_dev(synth.uniform(10000, 1, np.uint32))
+    with pytest.raises(gpu.MMSError):
+        gpu.sort_keys(t, kt=gpu.KEY_U32, tile_items=2048)
