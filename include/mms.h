@@ -124,6 +124,30 @@ mms_status mms_merge_pass(mms_key_type kt, const void* d_in, void* d_out, size_t
                           size_t run_len, int K, const int64_t* d_table, void* d_ws,
                           size_t ws_bytes, void* stream);
 
+/* ---- sorting without allocating -------------------------------------------- */
+
+/* No counterpart in the paper: a convenience for callers that cannot allocate
+ * device memory when they sort -- processes whose GPU memory belongs to
+ * another allocator that must not be bypassed, services with a fixed memory
+ * budget, or code that may not call cudaMalloc because it can synchronise the
+ * device.  mms_sort_keys_noalloc sorts n keys at d_keys in place exactly like
+ * mms_sort_keys, but its workspace is a fixed array of about 4 MiB that the
+ * library declares in device memory; every GPU that loads the library holds
+ * that array until the process exits.  The call allocates nothing.
+ *   - n must not exceed MMS_NOALLOC_MAX_KEYS_4B (u32, f32) or
+ *     MMS_NOALLOC_MAX_KEYS_8B (u64); larger n returns MMS_ERR_INVALID_ARG
+ *     and queues no work.
+ *   - The first call on a device looks up that device's copy of the array
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array: calls whose work overlaps on the GPU
+ *     (different streams, no ordering between them) race and corrupt each
+ *     other's results.  Order them on one stream or with events.
+ *   - Device-side error flags land in the array and are not reported. */
+#define MMS_NOALLOC_MAX_KEYS_4B ((size_t)1 << 20)
+#define MMS_NOALLOC_MAX_KEYS_8B ((size_t)1 << 19)
+mms_status mms_sort_keys_noalloc(mms_key_type kt, void* d_keys, size_t n, void* stream);
+
 /* ---- diagnostics ----------------------------------------------------------- */
 
 const char* mms_status_string(mms_status s);

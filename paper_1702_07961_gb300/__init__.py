@@ -18,7 +18,7 @@ import threading
 
 __all__ = ["load", "KEY_U32", "KEY_U64", "KEY_F32", "key_type_of", "sort_keys", "sort_pairs",
            "workspace_bytes", "tile_items", "plan", "tile_sort", "splitter_rows", "splitter",
-           "merge_pass", "workspace_status", "MMSError"]
+           "merge_pass", "workspace_status", "MMSError", "sort_keys_noalloc", "NOALLOC_MAX_KEYS"]
 
 KEY_U32, KEY_U64, KEY_F32 = 0, 1, 2
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -74,6 +74,8 @@ def load() -> ctypes.CDLL:
         L.mms_splitter.restype = i32
         L.mms_merge_pass.argtypes = [i32, vp, vp, sz, sz, i32, vp, vp, sz, vp]
         L.mms_merge_pass.restype = i32
+        L.mms_sort_keys_noalloc.argtypes = [i32, vp, sz, vp]
+        L.mms_sort_keys_noalloc.restype = i32
         L.mms_status_string.argtypes = [i32]
         L.mms_status_string.restype = ctypes.c_char_p
         L.mms_last_error_detail.argtypes = [ctypes.c_char_p, sz]
@@ -203,3 +205,25 @@ def merge_pass(inp, out, run_len: int, K: int, table, workspace=None, stream=Non
     _check(load().mms_merge_pass(kt, _ptr(inp), _ptr(out), inp.numel(), run_len, K, _ptr(table),
                                  ws_ptr, ws_len, _stream_handle(stream)))
     return out
+
+
+# Largest n mms_sort_keys_noalloc accepts, by key type (MMS_NOALLOC_MAX_KEYS_*).
+NOALLOC_MAX_KEYS = {KEY_U32: 1 << 20, KEY_F32: 1 << 20, KEY_U64: 1 << 19}
+
+
+def sort_keys_noalloc(keys, stream=None, kt: int | None = None):
+    """In-place sort that allocates no device memory (fixed library scratch).
+
+    For callers that cannot allocate device memory while they run.  Sizes up
+    to NOALLOC_MAX_KEYS[kt]; calls that overlap on the GPU race, since they
+    share one scratch array.
+    """
+    assert keys.is_cuda and keys.is_contiguous()
+    kt = key_type_of(keys) if kt is None else kt
+    n = keys.numel()
+    if n > NOALLOC_MAX_KEYS[kt]:
+        raise ValueError(f"sort_keys_noalloc takes at most {NOALLOC_MAX_KEYS[kt]} keys of this type, got {n}")
+    status = load().mms_sort_keys_noalloc(kt, _ptr(keys), n, _stream_handle(stream))
+    if status != 0:
+        raise MMSError(status, f"mms_sort_keys_noalloc failed: {load().mms_status_string(status).decode()}")
+    return keys
