@@ -44,6 +44,7 @@ def parse():
     p.add_argument("--n", type=int, default=DEFAULT_N)
     p.add_argument("--fanout", type=int, default=0, help="merge fanout K (0 = planner)")
     p.add_argument("--tile", type=int, default=0, help="tile items (0 = library default)")
+    p.add_argument("--pairs", action="store_true", help="key + uint32 index payload (stable key-value sort)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=1 << 25)
@@ -216,21 +217,33 @@ def main():
     keys_np = synth.permutation(N, 1 + rank)
     src = torch.from_numpy(keys_np.view(np.int32)).to(dev)
     work = torch.empty_like(src)
-    ws = torch.zeros(mms.workspace_bytes(mms.KEY_U32, N), dtype=torch.uint8, device=dev)
-    plan = mms.plan(mms.KEY_U32, N, args.fanout, args.tile)
-    n_ev = 2 + 2 * len(plan)
+    vals = torch.empty_like(src)
+    iota32 = torch.arange(N, dtype=torch.int32, device=dev)
+    ws = torch.zeros(mms.workspace_bytes(mms.KEY_U32, N, args.pairs), dtype=torch.uint8, device=dev)
+    plan = mms.plan(mms.KEY_U32, N, args.fanout, args.tile, pairs=args.pairs)
+    n_ev = 2 + 2 * len(plan) + (1 if args.pairs else 0)
     stream = torch.cuda.current_stream()
 
     def step(events=None):
         work.copy_(src)
-        mms.sort_keys(work, fanout=args.fanout, workspace=ws, kt=mms.KEY_U32, events=events,
-                      tile_items=args.tile)
+        if args.pairs:
+            vals.copy_(iota32)
+            mms.sort_pairs(work, vals, fanout=args.fanout, workspace=ws, kt=mms.KEY_U32, events=events,
+                           tile_items=args.tile)
+        else:
+            mms.sort_keys(work, fanout=args.fanout, workspace=ws, kt=mms.KEY_U32, events=events,
+                          tile_items=args.tile)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     iota = torch.arange(N, dtype=torch.int64, device=dev)
     verified = bool(torch.equal(work.to(torch.int64) & 0xFFFFFFFF, iota))
+    if args.pairs:
+        inv = torch.empty(N, dtype=torch.int64, device=dev)
+        inv[src.to(torch.int64) & 0xFFFFFFFF] = iota
+        verified = verified and bool(torch.equal(vals.to(torch.int64), inv))
+        del inv
     del iota
     mms.workspace_status(ws)
     if not verified:
@@ -263,12 +276,15 @@ def main():
     ms_per_step = total_ms / args.steps
     value = N * world / (ms_per_step / 1e3) / 1e9
 
-    # per-kernel averages over the timed steps: [tile_sort, (splitter, merge) per round]
+    # per-kernel averages over the timed steps: [tile_sort, (splitter, merge) per round,
+    # (value gather for pairs)]
     avg = [statistics.mean(s[i] for s in stage) for i in range(n_ev - 1)]
     tile_ms = avg[0]
     split_ms = [avg[1 + 2 * r] for r in range(len(plan))]
     merge_ms = [avg[2 + 2 * r] for r in range(len(plan))]
-    bytes_pass = 2 * N * KEY_BYTES
+    gather_ms = avg[-1] if args.pairs else None
+    # algorithmic bytes of one pass: every key (8-byte composite for pairs) read and written once
+    bytes_pass = 2 * N * (8 if args.pairs else KEY_BYTES)
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -280,6 +296,8 @@ def main():
     peak = peak or 6800.0
     merge_avg = statistics.mean(merge_ms) if merge_ms else None
     totals = {"tile_sort": tile_ms, "splitter": sum(split_ms), "merge_pass": sum(merge_ms)}
+    if gather_ms is not None:
+        totals["pairs_finalize"] = gather_ms
     dominant = max(totals, key=totals.get)
     if merge_avg:
         achieved = bytes_pass / (merge_avg / 1e3) / 1e9
@@ -297,20 +315,21 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"uniform random permutation of 0..N-1, N={N} uint32 keys, key-only "
-                               "(Sec. 6.3 'fully random'), one sort per step",
+        "config": {"workload": f"uniform random permutation of 0..N-1, N={N} uint32 keys, "
+                               + ("key + uint32 index payload (stable)" if args.pairs else "key-only")
+                               + " (Sec. 6.3 'fully random'), one sort per step",
                    "global_batch": N * world, "seq_len": None, "parallelism": f"replicas{world}",
                    "plan_fanouts": plan, "tile": args.tile or mms.tile_items(mms.KEY_U32),
                    "l2": "input 400 MB > 129 MB L2; a 400 MB copy restores the input between steps"},
         "stages_ms": {"tile_sort": tile_ms, "splitter": split_ms, "merge_pass": merge_ms,
-                      "dominant": dominant},
+                      "pairs_finalize": gather_ms, "dominant": dominant},
         "roofline": roofline,
-        "gpu_launches": args.steps * (1 + 2 * len(plan)),
+        "gpu_launches": args.steps * (1 + 2 * len(plan) + (1 if args.pairs else 0)),
         "verified_vs_closed_form": verified,
         "clocks": sampler.summary(t0, t1),
     }
 
-    if not args.no_e2e:
+    if not args.no_e2e and not args.pairs:
         # End to end: pinned host input -> device -> sort -> host, every step.
         h_in = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
         h_out = torch.empty_like(h_in).pin_memory()

@@ -77,10 +77,19 @@ mms_status mms_sort_keys(mms_key_type kt, void* d_keys, size_t n, void* d_ws, si
 mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws, size_t ws_bytes,
                             void* stream, const mms_options* opt);
 
-/* Sorts (key, 32-bit value) pairs stably by key; values move with keys.
- * Workspace: mms_sort_workspace_bytes(kt, n, 1). */
+/* Sorts (key, 32-bit value) pairs stably by key (Sec. 4 with the order of
+ * Sec. 4.1 read on (key, position)); values move with keys.  4-byte keys
+ * (u32, f32), n < 2^32.  The rounds run on unique 64-bit composites
+ * (ordered key << 32 | position) and a last kernel gathers the values.
+ * Workspace: mms_sort_workspace_bytes(kt, n, 1), or NULL (allocated and freed
+ * stream-ordered).  8-byte keys return MMS_ERR_UNSUPPORTED.  opt: as for
+ * mms_sort_keys_ex; its events are recorded before the value copy, after the
+ * base case, after each splitter and merge pass, and after the value gather;
+ * tile_items may be 0, 2048 or 4096 (composite tiles). */
 mms_status mms_sort_pairs(mms_key_type kt, void* d_keys, uint32_t* d_values, size_t n, void* d_ws,
                           size_t ws_bytes, void* stream);
+mms_status mms_sort_pairs_ex(mms_key_type kt, void* d_keys, uint32_t* d_values, size_t n,
+                             void* d_ws, size_t ws_bytes, void* stream, const mms_options* opt);
 
 /* Reads (synchronising with `stream`) and clears the workspace status word:
  * MMS_OK, MMS_ERR_TIMEOUT or MMS_ERR_INTERNAL. */

@@ -60,6 +60,8 @@ def load() -> ctypes.CDLL:
         L.mms_sort_keys_ex.restype = i32
         L.mms_sort_pairs.argtypes = [i32, vp, vp, sz, vp, sz, vp]
         L.mms_sort_pairs.restype = i32
+        L.mms_sort_pairs_ex.argtypes = [i32, vp, vp, sz, vp, sz, vp, ctypes.POINTER(_Options)]
+        L.mms_sort_pairs_ex.restype = i32
         L.mms_workspace_status.argtypes = [vp, sz, vp]
         L.mms_workspace_status.restype = i32
         L.mms_tile_items.argtypes = [i32]
@@ -136,7 +138,11 @@ def tile_items(kt: int) -> int:
     return int(load().mms_tile_items(kt))
 
 
-def plan(kt: int, n: int, fanout: int = 0, tile_items: int = 0):
+def plan(kt: int, n: int, fanout: int = 0, tile_items: int = 0, pairs: bool = False):
+    """Fanout of every merge round of a sort of n keys (of n pairs when `pairs`:
+    the rounds of a key-value sort run on 8-byte composites)."""
+    if pairs:
+        kt = KEY_U64
     buf = (ctypes.c_int * 64)()
     o = _opts(fanout, tile_items=tile_items)
     r = load().mms_plan(kt, n, ctypes.byref(o), buf, 64)
@@ -159,13 +165,16 @@ def sort_keys(keys, fanout: int = 0, workspace=None, stream=None, kt: int | None
     return keys
 
 
-def sort_pairs(keys, values, workspace=None, stream=None, kt: int | None = None):
-    """Stable sort of (key, 32-bit value) pairs in place."""
+def sort_pairs(keys, values, fanout: int = 0, workspace=None, stream=None, kt: int | None = None,
+               events=None, tile_items: int = 0):
+    """Stable sort of (key, 32-bit value) pairs in place (4-byte keys)."""
     assert keys.is_cuda and values.is_cuda and keys.numel() == values.numel()
+    assert keys.is_contiguous() and values.is_contiguous() and values.element_size() == 4
     kt = key_type_of(keys) if kt is None else kt
     ws_ptr, ws_len = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
-    _check(load().mms_sort_pairs(kt, _ptr(keys), _ptr(values), keys.numel(), ws_ptr, ws_len,
-                                 _stream_handle(stream)))
+    o = _opts(fanout, events, stream, tile_items)
+    _check(load().mms_sort_pairs_ex(kt, _ptr(keys), _ptr(values), keys.numel(), ws_ptr, ws_len,
+                                    _stream_handle(stream), ctypes.byref(o)))
     return keys, values
 
 

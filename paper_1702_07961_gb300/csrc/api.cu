@@ -33,17 +33,30 @@ size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct WsLayout {
   size_t keys_off, vals_off, table_off, total;
+  size_t comp0_off, comp1_off;   // key-value sort: the two 64-bit composite buffers
 };
 
+// Key-only sort: status | ping-pong copy of the keys | pivot table.
+// Key-value sort (4-byte keys): status | composites 0 | composites 1 | copy of
+// the values | pivot table (the rounds run on 8-byte composites).
 WsLayout ws_layout(mms_key_type kt, size_t n, int with_values) {
-  WsLayout L;
+  WsLayout L{};
   const size_t kb = (size_t)key_bytes_of(kt);
-  const size_t S = (kb == 8 ? 2048 : 4096);      // smallest tile a sort may use
-  L.keys_off = kStatusBytes;
-  L.vals_off = round_up(L.keys_off + n * kb, 256);
-  const size_t after_vals = L.vals_off + (with_values ? n * 4 : 0);
-  L.table_off = round_up(after_vals, 256);
-  const size_t rows = (n + S - 1) / S + 1;
+  if (!with_values) {
+    const size_t S = (kb == 8 ? 2048 : 4096);      // smallest tile a sort may use
+    L.keys_off = kStatusBytes;
+    L.vals_off = round_up(L.keys_off + n * kb, 256);
+    L.table_off = L.vals_off;
+    const size_t rows = (n + S - 1) / S + 1;
+    L.total = round_up(L.table_off + rows * mms::kMaxFanout * sizeof(long long), 256);
+    return L;
+  }
+  L.comp0_off = kStatusBytes;
+  L.comp1_off = round_up(L.comp0_off + n * 8, 256);
+  L.vals_off = round_up(L.comp1_off + n * 8, 256);
+  L.table_off = round_up(L.vals_off + n * 4, 256);
+  L.keys_off = L.comp0_off;
+  const size_t rows = (n + 2047) / 2048 + 1;
   L.total = round_up(L.table_off + rows * mms::kMaxFanout * sizeof(long long), 256);
   return L;
 }
@@ -218,10 +231,93 @@ mms_status mms_sort_keys(mms_key_type kt, void* d_keys, size_t n, void* d_ws, si
   return mms_sort_keys_ex(kt, d_keys, n, d_ws, ws_bytes, stream, nullptr);
 }
 
+mms_status mms_sort_pairs_ex(mms_key_type kt, void* d_keys, uint32_t* d_values, size_t n,
+                             void* d_ws, size_t ws_bytes, void* stream, const mms_options* opt) {
+  if (!valid_kt(kt)) return fail(MMS_ERR_INVALID_ARG, "unknown key type%s");
+  if (kt == MMS_KEY_U64)
+    return fail(MMS_ERR_UNSUPPORTED, "key-value sorting takes 4-byte keys (u32, f32)%s");
+  if (n <= 1) return MMS_OK;
+  if (n > 0xFFFFFFFEull) return fail(MMS_ERR_UNSUPPORTED, "key-value sorting takes fewer than 2^32 items%s");
+  if (!d_keys || !d_values || !aligned16(d_keys) || !aligned16(d_values))
+    return fail(MMS_ERR_INVALID_ARG, "keys/values pointer null or not 16-byte aligned%s");
+  if (opt && opt->fanout != 0 && (opt->fanout < 2 || opt->fanout > mms::kMaxFanout))
+    return fail(MMS_ERR_INVALID_ARG, "fanout must be 0 or in 2..32%s");
+  if (opt && opt->tile_items != 0 && opt->tile_items != 2048 && opt->tile_items != 4096)
+    return fail(MMS_ERR_INVALID_ARG, "tile_items of a key-value sort must be 0, 2048 or 4096%s");
+  const WsLayout L = ws_layout(kt, n, 1);
+  cudaStream_t s = (cudaStream_t)stream;
+  bool owned = false;
+  if (d_ws) {
+    if (!aligned16(d_ws)) return fail(MMS_ERR_INVALID_ARG, "workspace not 16-byte aligned%s");
+    if (ws_bytes < L.total) return fail(MMS_ERR_NO_MEMORY, "workspace smaller than mms_sort_workspace_bytes()%s");
+  } else {
+    cudaError_t e = cudaMallocAsync(&d_ws, L.total, s);
+    if (e != cudaSuccess) return fail(MMS_ERR_NO_MEMORY, "cudaMallocAsync of the workspace failed%s");
+    e = cudaMemsetAsync(d_ws, 0, kStatusBytes, s);
+    if (e != cudaSuccess) { cudaFreeAsync(d_ws, s); return cuda_fail(e, "workspace init"); }
+    owned = true;
+  }
+  unsigned char* ws = static_cast<unsigned char*>(d_ws);
+  int* dev_err = reinterpret_cast<int*>(ws);
+  void* comp[2] = {ws + L.comp0_off, ws + L.comp1_off};
+  void* vcopy = ws + L.vals_off;
+  long long* table = reinterpret_cast<long long*>(ws + L.table_off);
+  const bool is_f32 = kt == MMS_KEY_F32;
+
+  // The rounds run on 8-byte composites with the 8-byte tile geometry.
+  mms_options o8{};
+  if (opt) o8 = *opt;
+  const int tw = (opt && opt->tile_items) ? opt->tile_items / 1024 : mms::default_tile_warps(8);
+  o8.tile_items = 1024 * tw;
+  const long long S = 1024ll * tw;
+  int K[64];
+  const int rounds = plan_rounds(8, n, &o8, K, 64);
+
+  int ev = 0;
+  auto mark = [&]() {
+    if (opt && opt->events && ev < opt->num_events && opt->events[ev])
+      cudaEventRecord((cudaEvent_t)opt->events[ev], s);
+    ++ev;
+  };
+  mms_status st = MMS_OK;
+  mark();
+  cudaError_t ce = cudaMemcpyAsync(vcopy, d_values, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+  if (ce != cudaSuccess) st = cuda_fail(ce, "copy of the values");
+  if (st == MMS_OK)
+    st = check_launch(mms::launch_tile_sort_composite(tw, is_f32, d_keys, comp[0], (long long)n, s),
+                      "tile_sort (key-value)");
+  mark();
+  long long run_len = S;
+  int cur = 0;
+  for (int r = 0; r < rounds && st == MMS_OK; ++r) {
+    st = check_launch(mms::launch_splitter(8, S, comp[cur], (long long)n, run_len, K[r], table, s), "splitter");
+    mark();
+    if (st != MMS_OK) break;
+    st = check_launch(mms::launch_merge_pass(8, tw, false, comp[cur], comp[1 - cur], (long long)n,
+                                             run_len, K[r], table, dev_err, s), "merge_pass");
+    mark();
+    cur = 1 - cur;
+    run_len *= K[r];
+  }
+  if (st == MMS_OK)
+    st = check_launch(mms::launch_pairs_finalize(is_f32, comp[cur], vcopy, d_keys, d_values,
+                                                 (long long)n, s), "pairs_finalize");
+  mark();
+  if (owned) {
+    int word = 0;
+    cudaError_t e = cudaMemcpyAsync(&word, dev_err, sizeof word, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d_ws, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (st == MMS_OK && e != cudaSuccess) st = cuda_fail(e, "sort");
+    if (st == MMS_OK && word == mms::kDevErrTimeout) st = fail(MMS_ERR_TIMEOUT, "a device wait timed out%s");
+    else if (st == MMS_OK && word != 0) st = fail(MMS_ERR_INTERNAL, "device consistency check failed%s");
+  }
+  return st;
+}
+
 mms_status mms_sort_pairs(mms_key_type kt, void* d_keys, uint32_t* d_values, size_t n, void* d_ws,
                           size_t ws_bytes, void* stream) {
-  (void)kt; (void)d_keys; (void)d_values; (void)n; (void)d_ws; (void)ws_bytes; (void)stream;
-  return fail(MMS_ERR_UNSUPPORTED, "key-value sorting is not built yet%s");
+  return mms_sort_pairs_ex(kt, d_keys, d_values, n, d_ws, ws_bytes, stream, nullptr);
 }
 
 mms_status mms_tile_sort(mms_key_type kt, const void* d_in, void* d_out, size_t n, void* stream) {

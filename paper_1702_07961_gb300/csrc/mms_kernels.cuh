@@ -38,6 +38,16 @@ size_t merge_pass_smem_bytes(int key_bytes, int warps);
 cudaError_t launch_tile_sort(int key_bytes, int tile_warps, bool xin, bool xout, const void* in,
                              void* out, long long n, cudaStream_t s);
 
+// Base case of the key-value sort: 32-bit keys -> sorted tiles of 64-bit
+// composites (ordered key << 32 | array position).
+cudaError_t launch_tile_sort_composite(int tile_warps, bool xin, const void* keys32, void* out64,
+                                       long long n, cudaStream_t s);
+
+// Last step of the key-value sort: keys back from the sorted composites, and
+// each value gathered from its original position.
+cudaError_t launch_pairs_finalize(bool xout, const void* comp64, const void* vals_src,
+                                  void* keys_out, void* vals_out, long long n, cudaStream_t s);
+
 // Splitter: co-ranks of every output tile start (tiles of S items) of every
 // group of K runs.
 cudaError_t launch_splitter(int key_bytes, long long S, const void* in, long long n,

@@ -98,44 +98,15 @@ __device__ __forceinline__ void cta_store_tile(const KeyT* src, KeyT* dst, int m
   for (int i = body + (int)threadIdx.x; i < m; i += blockDim.x) dst[i] = src[i];
 }
 
-template <typename KeyT, int WARPS, bool XIN, bool XOUT>
-__global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
-    tile_sort_kernel(const KeyT* __restrict__ in, KeyT* out, long long n) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
+// Everything after the load: warp sorts, CTA merge levels, store of the tile.
+template <typename KeyT, int WARPS, bool XOUT>
+__device__ __forceinline__ void tile_sort_finish(KeyT (&v)[32], KeyT* out, long long n,
+                                                 long long base, unsigned char* smem_raw) {
   constexpr int T = WARPS * kBlockItems;
   KeyT* bufX = reinterpret_cast<KeyT*>(smem_raw);
   KeyT* bufY = bufX + T;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   KeyT* scr = bufY + T + warp * Scratch<KeyT>::ITEMS;
-
-  const long long base = (long long)blockIdx.x * T;
-  const long long wbase = base + (long long)warp * kBlockItems;
-  const long long rem = n - wbase;
-  const int cnt = rem <= 0 ? 0 : (rem >= kBlockItems ? kBlockItems : (int)rem);
-
-  using V = Vec16<KeyT>;
-  constexpr int NV = 32 / V::E;          // 16-byte vectors per lane
-  KeyT v[32];
-  if (cnt == kBlockItems) {
-    const typename V::T* src = reinterpret_cast<const typename V::T*>(in + wbase);
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      const typename V::T x = __ldg(src + q * 32 + lane);
-      KeyT t[V::E];
-      V::unpack(x, t);
-#pragma unroll
-      for (int c = 0; c < V::E; ++c) v[q * V::E + c] = xform_in<KeyT, XIN>(t[c]);
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-#pragma unroll
-      for (int c = 0; c < V::E; ++c) {
-        const int e = q * 32 * V::E + lane * V::E + c;
-        v[q * V::E + c] = e < cnt ? xform_in<KeyT, XIN>(in[wbase + e]) : key_pad<KeyT>();
-      }
-    }
-  }
 
   warp_sort_1024(v, lane);
   const long long trem = n - base;
@@ -171,6 +142,89 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
   cta_store_tile(src, out + base, m);
 }
 
+template <typename KeyT, int WARPS, bool XIN, bool XOUT>
+__global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
+    tile_sort_kernel(const KeyT* __restrict__ in, KeyT* out, long long n) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  constexpr int T = WARPS * kBlockItems;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long base = (long long)blockIdx.x * T;
+  const long long wbase = base + (long long)warp * kBlockItems;
+  const long long rem = n - wbase;
+  const int cnt = rem <= 0 ? 0 : (rem >= kBlockItems ? kBlockItems : (int)rem);
+
+  using V = Vec16<KeyT>;
+  constexpr int NV = 32 / V::E;          // 16-byte vectors per lane
+  KeyT v[32];
+  if (cnt == kBlockItems) {
+    const typename V::T* src = reinterpret_cast<const typename V::T*>(in + wbase);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const typename V::T x = __ldg(src + q * 32 + lane);
+      KeyT t[V::E];
+      V::unpack(x, t);
+#pragma unroll
+      for (int c = 0; c < V::E; ++c) v[q * V::E + c] = xform_in<KeyT, XIN>(t[c]);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+#pragma unroll
+      for (int c = 0; c < V::E; ++c) {
+        const int e = q * 32 * V::E + lane * V::E + c;
+        v[q * V::E + c] = e < cnt ? xform_in<KeyT, XIN>(in[wbase + e]) : key_pad<KeyT>();
+      }
+    }
+  }
+  tile_sort_finish<KeyT, WARPS, XOUT>(v, out, n, base, smem_raw);
+}
+
+// Base case of the key-value sort: 32-bit keys (floats through the order
+// transform when XIN) are read and turned into unique 64-bit composites
+// (ordered key << 32 | position in the array), whose ascending order is the
+// stable key order; tiles of composites are then sorted like 64-bit keys.
+template <int WARPS, bool XIN>
+__global__ void __launch_bounds__(WARPS * 32, (MinBlocks<uint64_t, WARPS>::value))
+    tile_sort_composite_kernel(const uint32_t* __restrict__ in, uint64_t* out, long long n) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  constexpr int T = WARPS * kBlockItems;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long base = (long long)blockIdx.x * T;
+  const long long wbase = base + (long long)warp * kBlockItems;
+  const long long rem = n - wbase;
+  const int cnt = rem <= 0 ? 0 : (rem >= kBlockItems ? kBlockItems : (int)rem);
+  uint64_t v[32];
+  if (cnt == kBlockItems) {
+    const uint4* src = reinterpret_cast<const uint4*>(in + wbase);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint4 x = __ldg(src + q * 32 + lane);
+      const uint32_t k[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint32_t key = XIN ? f32_to_ordered(k[c]) : k[c];
+        const uint64_t pos = (uint64_t)(wbase + q * 128 + lane * 4 + c);
+        v[q * 4 + c] = ((uint64_t)key << 32) | pos;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int e = q * 128 + lane * 4 + c;
+        uint64_t x = key_pad<uint64_t>();
+        if (e < cnt) {
+          const uint32_t key = XIN ? f32_to_ordered(in[wbase + e]) : in[wbase + e];
+          x = ((uint64_t)key << 32) | (uint64_t)(wbase + e);
+        }
+        v[q * 4 + c] = x;
+      }
+    }
+  }
+  tile_sort_finish<uint64_t, WARPS, false>(v, out, n, base, smem_raw);
+}
+
 size_t tile_sort_smem_bytes(int key_bytes, int warps) {
   const size_t scratch = key_bytes == 8 ? Scratch<uint64_t>::ITEMS : Scratch<uint32_t>::ITEMS;
   return (size_t)key_bytes * (2 * warps * kBlockItems + warps * scratch);
@@ -191,12 +245,36 @@ static cudaError_t launch_tile_sort_t(const void* in, void* out, long long n, cu
 template <int WARPS>
 static cudaError_t launch_tile_sort_w(int key_bytes, bool xin, bool xout, const void* in, void* out,
                                       long long n, cudaStream_t s) {
+  if (key_bytes == 8 && WARPS == 8) return cudaErrorInvalidValue;
   if (key_bytes == 4) {
     if (xin && xout) return launch_tile_sort_t<uint32_t, WARPS, true, true>(in, out, n, s);
     if (xin) return launch_tile_sort_t<uint32_t, WARPS, true, false>(in, out, n, s);
     return launch_tile_sort_t<uint32_t, WARPS, false, false>(in, out, n, s);
   }
-  return launch_tile_sort_t<uint64_t, WARPS, false, false>(in, out, n, s);
+  if constexpr (WARPS != 8) return launch_tile_sort_t<uint64_t, WARPS, false, false>(in, out, n, s);
+  return cudaErrorInvalidValue;
+}
+
+template <int WARPS, bool XIN>
+static cudaError_t launch_composite_t(const void* in, void* out, long long n, cudaStream_t s) {
+  const size_t smem = tile_sort_smem_bytes(8, WARPS);
+  auto k = tile_sort_composite_kernel<WARPS, XIN>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long T = (long long)WARPS * kBlockItems;
+  const unsigned grid = (unsigned)((n + T - 1) / T);
+  k<<<grid, WARPS * 32, smem, s>>>(static_cast<const uint32_t*>(in), static_cast<uint64_t*>(out), n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_sort_composite(int tile_warps, bool xin, const void* keys32, void* out64,
+                                       long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (tile_warps == 4)
+    return xin ? launch_composite_t<4, true>(keys32, out64, n, s) : launch_composite_t<4, false>(keys32, out64, n, s);
+  if (tile_warps == 2)
+    return xin ? launch_composite_t<2, true>(keys32, out64, n, s) : launch_composite_t<2, false>(keys32, out64, n, s);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tile_sort(int key_bytes, int tile_warps, bool xin, bool xout, const void* in,

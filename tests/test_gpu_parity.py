@@ -237,6 +237,72 @@ def test_workspace_too_small_is_rejected(gpu):
         gpu.sort_keys(t, workspace=ws, kt=gpu.KEY_U32)
 
 
+# ---- key-value sort (stable) -------------------------------------------------------
+
+def gpu_sort_pairs(mms, keys, vals, fanout=0, tile=0):
+    kt = kt_of(keys.dtype, mms)
+    tk, tv = to_dev(keys), to_dev(vals)
+    mms.sort_pairs(tk, tv, fanout=fanout, kt=kt, tile_items=tile)
+    return to_host(tk, keys.dtype), to_host(tv, np.uint32)
+
+
+@pytest.mark.parametrize("n", [2, 3, 1000, 4096, 4097, 4096 * 23 + 5, 1 << 20])
+def test_pairs_u32_index_payload_stable(gpu, n):
+    keys = synth.uniform(n, n, np.uint32) % np.uint32(max(2, n // 7))   # many equal keys
+    vals = synth.index_payload(n)
+    wk, wv = oracle.sort(keys, vals)
+    gk, gv = gpu_sort_pairs(gpu, keys, vals)
+    assert_bits_equal(gk, wk)
+    assert_bits_equal(gv, wv)
+
+
+@pytest.mark.parametrize("fanout,tile", [(2, 0), (4, 2048), (8, 4096), (32, 0)])
+def test_pairs_u32_random_payload(gpu, fanout, tile):
+    n = 4096 * 41 + 333
+    keys = synth.uniform(n, 17, np.uint32) % np.uint32(5000)
+    vals = synth.uniform(n, 18, np.uint32)
+    wk, wv = oracle.sort(keys, vals)
+    gk, gv = gpu_sort_pairs(gpu, keys, vals, fanout, tile)
+    assert_bits_equal(gk, wk)
+    assert_bits_equal(gv, wv)
+
+
+def test_pairs_f32_specials(gpu):
+    n = 4096 * 9 + 71
+    keys = synth.normal_f32(n, 19)
+    keys[::5] = keys[1::5][: keys[::5].size]              # repeated floats, NaNs and -0.0 included
+    vals = synth.index_payload(n)
+    wk, wv = oracle.sort(keys, vals)
+    gk, gv = gpu_sort_pairs(gpu, keys, vals)
+    assert_bits_equal(gk, wk)
+    assert_bits_equal(gv, wv)
+
+
+def test_pairs_u64_is_unsupported(gpu):
+    tk = to_dev(synth.uniform(100, 1, np.uint64))
+    tv = to_dev(synth.index_payload(100))
+    with pytest.raises(gpu.MMSError):
+        gpu.sort_pairs(tk, tv, kt=gpu.KEY_U64)
+
+
+@pytest.mark.slow
+def test_full_size_pairs_permutation_1e8(gpu):
+    """10^8 uint32 keys, permutation of 0..N-1, index payload: keys sort to iota
+    and the payload becomes the inverse permutation (closed form)."""
+    import torch
+    n = 10**8
+    keys = synth.permutation(n, 5)
+    tk = to_dev(keys)
+    tv = torch.arange(n, dtype=torch.int32, device="cuda")
+    gpu.sort_pairs(tk, tv, kt=gpu.KEY_U32)
+    iota = torch.arange(n, dtype=torch.int64, device="cuda")
+    assert torch.equal(tk.to(torch.int64) & 0xFFFFFFFF, iota)
+    src = torch.from_numpy(keys.view(np.int32)).cuda().to(torch.int64) & 0xFFFFFFFF
+    inv = torch.empty(n, dtype=torch.int64, device="cuda")
+    inv[src] = iota
+    assert torch.equal(tv.to(torch.int64), inv)
+
+
 # ---- full-size configurations: closed forms ----------------------------------------
 
 @pytest.mark.slow
