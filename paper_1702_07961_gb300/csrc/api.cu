@@ -67,29 +67,23 @@ int tile_warps_for(int key_bytes, const mms_options* opt) {
   return mms::default_tile_warps(key_bytes);
 }
 
-// Fanout of every round.  Auto: as few rounds as K <= 32 allows, with the
-// log2 K levels spread evenly (Sec. 6.2 avoids a last round merging fewer
-// than K lists by resizing the base case; spreading the levels serves the
-// same end without changing the tile).
+// Fanout of every round.  Auto: the fanout measured fastest on GB300 for the
+// key width (K = 4 for 4-byte keys, K = 8 for 8-byte keys and composites; on
+// this GPU the on-chip merge levels, not HBM traffic, set the pace, so fewer
+// levels per round beat fewer rounds).  Sec. 6.2 tunes K per platform the
+// same way.  The rounds are ceil(log_K(runs)).
 int plan_rounds(int key_bytes, size_t n, const mms_options* opt, int* K, int maxr) {
   const long long S = 1024ll * tile_warps_for(key_bytes, opt);
   const long long runs = ((long long)n + S - 1) / S;
   if (runs <= 1) return 0;
-  int levels = 0;
-  while ((1ll << levels) < runs) ++levels;
+  const int fanout = (opt && opt->fanout >= 2) ? opt->fanout : (key_bytes == 8 ? 8 : 4);
   int rounds = 0;
-  if (opt && opt->fanout >= 2) {
-    long long cover = 1;
-    while (cover < runs) {
-      cover *= opt->fanout;
-      if (rounds < maxr) K[rounds] = opt->fanout;
-      ++rounds;
-    }
-    return rounds;
+  long long cover = 1;
+  while (cover < runs) {
+    cover *= fanout;
+    if (rounds < maxr) K[rounds] = fanout;
+    ++rounds;
   }
-  rounds = (levels + 4) / 5;
-  const int base = levels / rounds, extra = levels % rounds;
-  for (int i = 0; i < rounds && i < maxr; ++i) K[i] = 1 << (base + (i < extra ? 1 : 0));
   return rounds;
 }
 
