@@ -144,7 +144,7 @@ def run_reference(args):
     import numpy as np
     import synth
     n_sample = min(args.n, 1 << 22)
-    keys = synth.permutation(args.n if args.n <= (1 << 24) else n_sample, 1)[:n_sample]
+    keys = synth.permutation(args.n, 1)[:n_sample].copy()      # first keys of the GPU arm's workload
     import oracle
     for _ in range(args.warmup):
         oracle.sort(keys)
@@ -173,6 +173,18 @@ def run_reference(args):
 
 
 # ---- the GPU arm --------------------------------------------------------------------
+
+def aggregate_over_ranks(total_ms: float, keys_per_rank: int, steps: int, world: int, device=None):
+    """Replicas: every rank sorts its own array.  Returns (ms per step of the
+    slowest rank, Gkeys/s of the whole job = all ranks' keys / that time)."""
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item()) / steps
+    return ms, keys_per_rank * world / (ms / 1e3) / 1e9
+
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
@@ -268,13 +280,7 @@ def main():
 
     step_ms = [e[0].elapsed_time(e[-1]) for e in evs]
     stage = [[e[i].elapsed_time(e[i + 1]) for i in range(n_ev - 1)] for e in evs]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = N * world / (ms_per_step / 1e3) / 1e9
+    ms_per_step, value = aggregate_over_ranks(sum(step_ms), N, args.steps, world, dev)
 
     # per-kernel averages over the timed steps: [tile_sort, (splitter, merge) per round,
     # (value gather for pairs)]
