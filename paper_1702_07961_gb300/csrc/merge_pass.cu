@@ -9,12 +9,13 @@
 //      (cp.async.bulk, one mbarrier; the < 16-byte ragged ends of each
 //      segment by plain loads), so every input byte is read from HBM once;
 //   2. merges them along a binary merge tree of ceil(log2 K) levels (the
-//      paper's minBlockHeap has the same levels).  Every tree node (a pair of
-//      sequences) is cut into 1024-item output blocks; warps take blocks from
-//      a shared counter in level order and wait only for the two child nodes
-//      of their block, not for whole levels.  A node's output is written into
-//      the span its segments were staged in, alternating between two buffers
-//      by level, so no block can overwrite data another block still reads.
+//      paper's minBlockHeap has the same levels), one level at a time: every
+//      tree node of the level (a pair of sequences) is cut into 1024-item
+//      output blocks, the blocks of the level are dealt to the warps, and a
+//      CTA barrier separates the levels.  A node's output is written into the
+//      span its segments were staged in, alternating between two buffers by
+//      level; every segment span carries 32 items of slack so that a node's
+//      last, partial block can use its output region as transpose space.
 //      Each block is merged by the conflict-free warp bitonic block merge;
 //   3. writes the tile with one TMA bulk store, so every output byte is
 //      written once: 2 * S * sizeof(key) bytes of HBM traffic per tile.
@@ -23,50 +24,35 @@
 
 namespace mms {
 
-// Shared-memory geometry of a merge CTA.  X: the staged segments, each at a
-// 16-byte aligned span start R_r (up to 2E-2 items of slack per segment), and
-// the even tree levels' outputs; Y: the odd levels' outputs (same spans).
+// Shared-memory geometry of a merge CTA for fanout K.  X: the staged
+// segments, each at a 16-byte aligned span start R_r (up to 2E-2 items of
+// alignment slack and 32 items of transpose slack per segment), and the odd
+// tree levels' inputs; Y: the same spans, one buffer per level parity.
 template <typename KeyT, int WARPS>
 struct MergeGeom {
   static constexpr int E = Vec16<KeyT>::E;
   static constexpr int S = WARPS * kBlockItems;
-  static constexpr int CAP = S + kMaxFanout * 2 * E + E;
-  static constexpr size_t SCRATCH_OFF = sizeof(KeyT) * 2 * (size_t)CAP;
-  static constexpr size_t CTRL_OFF =
-      SCRATCH_OFF + sizeof(KeyT) * (size_t)WARPS * Scratch<KeyT>::ITEMS;
-  // control block: mbarrier (8), next item (4), error flag (4), done[32] (128)
-  static constexpr size_t BYTES = CTRL_OFF + 8 + 4 + 4 + 4 * 32;
+  static constexpr int kSlack = 32;
+  __host__ __device__ static constexpr int cap(int K) { return S + K * (2 * E + kSlack) + E; }
+  // control block: mbarrier (8), error flag (4), pad (4)
+  __host__ __device__ static constexpr size_t bytes(int K) {
+    return sizeof(KeyT) * 2 * (size_t)cap(K) + 16;
+  }
 };
 
-size_t merge_pass_smem_bytes(int key_bytes, int warps) {
+size_t merge_pass_smem_bytes(int key_bytes, int warps, int K) {
   if (key_bytes == 4) {
     switch (warps) {
-      case 4: return MergeGeom<uint32_t, 4>::BYTES;
-      case 8: return MergeGeom<uint32_t, 8>::BYTES;
+      case 4: return MergeGeom<uint32_t, 4>::bytes(K);
+      case 8: return MergeGeom<uint32_t, 8>::bytes(K);
     }
   } else {
     switch (warps) {
-      case 2: return MergeGeom<uint64_t, 2>::BYTES;
-      case 4: return MergeGeom<uint64_t, 4>::BYTES;
+      case 2: return MergeGeom<uint64_t, 2>::bytes(K);
+      case 4: return MergeGeom<uint64_t, 4>::bytes(K);
     }
   }
   return 0;
-}
-
-// Bounded wait until tree node `c` has all `nb` of its blocks written; gives
-// up after about two seconds, or at once when another warp has given up.
-__device__ __forceinline__ bool wait_node(const int* done, const int* err_flag, int c, int nb) {
-  if (c < 0) return true;
-  const volatile int* d = done;
-  const volatile int* ef = err_flag;
-  if (d[c] >= nb) return true;
-  const long long t0 = clock64();
-  for (long long it = 0; it < (1ll << 26); ++it) {
-    __nanosleep(32);
-    if (d[c] >= nb) return true;
-    if (*ef != 0 || clock64() - t0 > 4000000000ll) break;
-  }
-  return false;
 }
 
 template <typename KeyT, int WARPS, bool XOUT>
@@ -78,14 +64,11 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
   constexpr int E = G::E;
   constexpr int S = G::S;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int cap = G::cap(K);
   KeyT* bufX = reinterpret_cast<KeyT*>(smem_raw);
-  KeyT* bufY = bufX + G::CAP;
+  KeyT* bufY = bufX + cap;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  KeyT* scr = reinterpret_cast<KeyT*>(smem_raw + G::SCRATCH_OFF) + warp * Scratch<KeyT>::ITEMS;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + G::CTRL_OFF);
-  int* next_item = reinterpret_cast<int*>(smem_raw + G::CTRL_OFF + 8);
-  int* err_flag = next_item + 1;
-  int* done = next_item + 2;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + sizeof(KeyT) * 2 * (size_t)cap);
 
   const long long t = blockIdx.x;
   const long long g = t / tpg, j = t % tpg;
@@ -121,7 +104,7 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
   const long long gsrc = rstart + lo;                  // first item, global index
   const int len = act ? (int)(hi - lo) : 0;
   const int head = act ? (int)(gsrc % E) : 0;          // items copied before the segment
-  const int span = (head + len + E - 1) / E * E;       // staged span, multiple of E
+  const int span = (head + len + E - 1) / E * E + G::kSlack;   // staged span + transpose slack
   int incl = span;
   int lincl = len;
 #pragma unroll
@@ -141,12 +124,7 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
   const unsigned bulk_bytes =
       (act && bulk_hi > bulk_lo) ? (unsigned)((bulk_hi - bulk_lo) * sizeof(KeyT)) : 0u;
 
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    *next_item = 0;
-    *err_flag = 0;
-  }
-  if (threadIdx.x < 32) done[threadIdx.x] = 0;
+  if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
   if (warp == 0) {
     unsigned total = bulk_bytes;
@@ -172,19 +150,15 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
   // Merge-tree nodes, one per lane, in level order: node (level l >= 1, pair q)
   // merges child A = segments [q*2^l, q*2^l + 2^(l-1)) and child B = the rest
   // of [q*2^l, (q+1)*2^l) (clipped to K).  Every warp derives the same table.
-  int nl = 0, nnodes = 0, c_level = 0, c_pair = 0, prev_start = 0, prev_count = 0;
+  int nl = 0, nnodes = 0, c_level = 0, c_pair = 0;
   {
-    int cnt = K, idx = 0, pidx = 0, pcnt = K;
+    int cnt = K, idx = 0;
     for (int l = 1; cnt > 1; ++l) {
       const int pairs = (cnt + 1) >> 1;
       if (lane >= idx && lane < idx + pairs) {
         c_level = l;
         c_pair = lane - idx;
-        prev_start = pidx;                              // first node of level l-1
-        prev_count = pcnt;                              // sequences of level l-1
       }
-      pidx = idx;
-      pcnt = pairs;
       idx += pairs;
       cnt = pairs;
       nl = l;
@@ -217,11 +191,7 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
     const int x = __shfl_up_sync(0xffffffffu, c_first, o);
     if (lane >= o) c_first += x;
   }
-  const int total_items = __shfl_sync(0xffffffffu, c_first, (nnodes - 1) & 31);
   c_first -= c_nb;
-  const int c_depA = (c_level >= 2) ? prev_start + 2 * c_pair : -1;
-  const int c_depB =
-      (c_level >= 2 && 2 * c_pair + 1 < prev_count) ? prev_start + 2 * c_pair + 1 : -1;
 
   const bool ok = mbar_wait_bounded(bar, 0);
   if (__syncthreads_or(!ok)) {
@@ -229,55 +199,37 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
     return;
   }
 
-  for (;;) {
-    int item = 0;
-    if (lane == 0) item = atomicAdd(next_item, 1);
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= total_items) break;
-    const unsigned sel = __ballot_sync(0xffffffffu, is_node && c_first <= item && c_nb > 0);
-    const int c = 31 - __clz(sel);
-    const int level = __shfl_sync(0xffffffffu, c_level, c);
-    const int lenA = __shfl_sync(0xffffffffu, c_lenA, c);
-    const int lenB = __shfl_sync(0xffffffffu, c_lenB, c);
-    const int offA = __shfl_sync(0xffffffffu, c_offA, c);
-    const int offB = __shfl_sync(0xffffffffu, c_offB, c);
-    const int outo = __shfl_sync(0xffffffffu, c_out, c);
-    const int fi = __shfl_sync(0xffffffffu, c_first, c);
-    const int depA = __shfl_sync(0xffffffffu, c_depA, c);
-    const int depB = __shfl_sync(0xffffffffu, c_depB, c);
-    const int nbA = __shfl_sync(0xffffffffu, c_nb, depA & 31);
-    const int nbB = __shfl_sync(0xffffffffu, c_nb, depB & 31);
-    int ready = 1;
-    if (lane == 0)
-      ready = wait_node(done, err_flag, depA, nbA) && wait_node(done, err_flag, depB, nbB);
-    ready = __shfl_sync(0xffffffffu, ready, 0);
-    if (!ready) {
-      if (lane == 0) atomicExch(err_flag, 1);
-      continue;
+  // Level by level: the blocks of every node of level lv are dealt to the
+  // warps round-robin; a barrier ends the level.
+  for (int lv = 1; lv <= nl; ++lv) {
+    const unsigned lvm = __ballot_sync(0xffffffffu, is_node && c_level == lv);
+    const int n0 = __ffs(lvm) - 1, n1 = 31 - __clz(lvm);
+    const int it0 = __shfl_sync(0xffffffffu, c_first, n0);
+    const int it1 = __shfl_sync(0xffffffffu, c_first + c_nb, n1);
+    const KeyT* src = (lv & 1) ? bufX : bufY;           // level lv reads level lv-1's buffer
+    KeyT* dst = (lv & 1) ? bufY : bufX;
+    for (int item = it0 + warp; item < it1; item += WARPS) {
+      const unsigned sel = __ballot_sync(0xffffffffu, is_node && c_first <= item && c_nb > 0);
+      const int c = 31 - __clz(sel);
+      const int lenA = __shfl_sync(0xffffffffu, c_lenA, c);
+      const int lenB = __shfl_sync(0xffffffffu, c_lenB, c);
+      const int offA = __shfl_sync(0xffffffffu, c_offA, c);
+      const int offB = __shfl_sync(0xffffffffu, c_offB, c);
+      const int outo = __shfl_sync(0xffffffffu, c_out, c);
+      const int fi = __shfl_sync(0xffffffffu, c_first, c);
+      const KeyT* A = src + offA;
+      const KeyT* B = src + offB;
+      const int L = lenA + lenB;
+      const int d0 = (item - fi) * kBlockItems;
+      const int m = (L - d0) < kBlockItems ? (L - d0) : kBlockItems;
+      const int a0 = warp_corank(A, lenA, B, lenB, d0, lane);
+      const int a1 = (d0 + m == L) ? lenA : warp_corank(A, lenA, B, lenB, d0 + m, lane);
+      const int X = a1 - a0;
+      warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, lane,
+                             XOUT && lv == nl);
+      __syncwarp();
     }
-    __threadfence_block();
-    const KeyT* src = (level & 1) ? bufX : bufY;        // level l reads level l-1's buffer
-    KeyT* dst = (level & 1) ? bufY : bufX;
-    const KeyT* A = src + offA;
-    const KeyT* B = src + offB;
-    const int L = lenA + lenB;
-    const int d0 = (item - fi) * kBlockItems;
-    const int m = (L - d0) < kBlockItems ? (L - d0) : kBlockItems;
-    const int a0 = warp_corank(A, lenA, B, lenB, d0, lane);
-    const int a1 = (d0 + m == L) ? lenA : warp_corank(A, lenA, B, lenB, d0 + m, lane);
-    const int X = a1 - a0;
-    warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, scr, lane,
-                           XOUT && level == nl);
-    __syncwarp();
-    if (lane == 0) {
-      __threadfence_block();
-      atomicAdd(&done[c], 1);
-    }
-  }
-  __syncthreads();
-  if (*err_flag) {
-    if (threadIdx.x == 0) set_device_error(dev_err, kDevErrTimeout);
-    return;
+    __syncthreads();
   }
   // The root node's output is the tile, at span start 0 of the last level's buffer.
   const KeyT* res = (nl & 1) ? bufY : bufX;
@@ -293,7 +245,7 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
 template <typename KeyT, int WARPS, bool XOUT>
 static cudaError_t launch_merge_t(const void* in, void* out, long long n, long long run_len, int K,
                                   const long long* table, int* dev_err, cudaStream_t s) {
-  const size_t smem = MergeGeom<KeyT, WARPS>::BYTES;
+  const size_t smem = MergeGeom<KeyT, WARPS>::bytes(K);
   auto k = merge_pass_kernel<KeyT, WARPS, XOUT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -4,10 +4,10 @@
 // warp co-rank (merge-path) search in shared memory, and TMA/mbarrier PTX.
 //
 // Shared-memory discipline (Sec. 3.2 and Sec. 5.2): every shared-memory access
-// a warp makes is 32 consecutive items (any base: one bank each), a row of a
-// padded table read with 16-byte vectors whose rows start 4 banks apart, a
-// 16-byte chunk whose position is XOR-permuted by the lane id, or a probe at an
-// odd stride -- never a data-dependent gather -- so no input can cause a bank
+// a warp makes is 32 consecutive items (any base: one bank each), a row of 32
+// items whose 16-byte chunks are XOR-swizzled by the row index, a 16-byte
+// chunk whose position is XOR-permuted by the lane id, or a probe at an odd
+// stride -- never a data-dependent gather -- so no input can cause a bank
 // conflict.
 #pragma once
 
@@ -61,20 +61,20 @@ struct Vec16<uint64_t> {
   __device__ static ulonglong2 pack(const uint64_t* o) { return make_ulonglong2(o[0], o[1]); }
 };
 
-// Per-warp transpose scratch: 32 rows, each padded so that consecutive rows
-// start 4 banks apart (u32: 36 words; u64: 34 items = 68 words), which makes
-// both the row-wise 16-byte vector reads and the column-wise scalar writes
-// conflict-free.
-template <typename KeyT>
-struct Scratch {
-  static constexpr int ROW = sizeof(KeyT) == 4 ? 36 : 34;
-  static constexpr int ITEMS = 32 * ROW;
-};
+// Compare-exchange as one min and one max (no compare-and-select pair).
+__device__ __forceinline__ uint32_t kmin(uint32_t a, uint32_t b) { return min(a, b); }
+__device__ __forceinline__ uint32_t kmax(uint32_t a, uint32_t b) { return max(a, b); }
+__device__ __forceinline__ uint64_t kmin(uint64_t a, uint64_t b) {
+  return min((unsigned long long)a, (unsigned long long)b);
+}
+__device__ __forceinline__ uint64_t kmax(uint64_t a, uint64_t b) {
+  return max((unsigned long long)a, (unsigned long long)b);
+}
 
 template <typename KeyT>
 __device__ __forceinline__ void cas(KeyT& a, KeyT& b) {
-  const KeyT lo = a < b ? a : b;
-  const KeyT hi = a < b ? b : a;
+  const KeyT lo = kmin(a, b);
+  const KeyT hi = kmax(a, b);
   a = lo;
   b = hi;
 }
@@ -85,10 +85,9 @@ __device__ __forceinline__ void cas(KeyT& a, KeyT& b) {
 // that mask, which makes the following shared-memory store conflict-free.
 template <typename KeyT>
 __device__ __forceinline__ void cas_dir(KeyT& a, KeyT& b, bool flip) {
-  const KeyT lo = a < b ? a : b;
-  const KeyT hi = a < b ? b : a;
-  a = flip ? hi : lo;
-  b = flip ? lo : hi;
+  const KeyT x = a, y = b;
+  a = flip ? kmax(x, y) : kmin(x, y);
+  b = flip ? kmin(x, y) : kmax(x, y);
 }
 
 template <typename KeyT>
@@ -103,18 +102,35 @@ __device__ __forceinline__ uint32_t smem_u32addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void lds_pred(uint32_t& v, const uint32_t* p, bool pred) {
+// Loads p[0] into v when idx < lim (signed), in one compare and one predicated
+// load; v keeps its value otherwise.
+__device__ __forceinline__ void lds_if_lt(uint32_t& v, const uint32_t* p, int idx, int lim) {
   asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q ld.shared.b32 %0, [%1];\n\t}\n"
+      "{\n\t.reg .pred q;\n\tsetp.lt.s32 q, %2, %3;\n\t@q ld.shared.b32 %0, [%1];\n\t}\n"
       : "+r"(v)
-      : "r"(smem_u32addr(p)), "r"((int)pred)
+      : "r"(smem_u32addr(p)), "r"(idx), "r"(lim)
       : "memory");
 }
-__device__ __forceinline__ void lds_pred(uint64_t& v, const uint64_t* p, bool pred) {
+__device__ __forceinline__ void lds_if_lt(uint64_t& v, const uint64_t* p, int idx, int lim) {
   asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q ld.shared.b64 %0, [%1];\n\t}\n"
+      "{\n\t.reg .pred q;\n\tsetp.lt.s32 q, %2, %3;\n\t@q ld.shared.b64 %0, [%1];\n\t}\n"
       : "+l"(v)
-      : "r"(smem_u32addr(p)), "r"((int)pred)
+      : "r"(smem_u32addr(p)), "r"(idx), "r"(lim)
+      : "memory");
+}
+// Loads p[0] into v when idx >= lim (signed).
+__device__ __forceinline__ void lds_if_ge(uint32_t& v, const uint32_t* p, int idx, int lim) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ge.s32 q, %2, %3;\n\t@q ld.shared.b32 %0, [%1];\n\t}\n"
+      : "+r"(v)
+      : "r"(smem_u32addr(p)), "r"(idx), "r"(lim)
+      : "memory");
+}
+__device__ __forceinline__ void lds_if_ge(uint64_t& v, const uint64_t* p, int idx, int lim) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ge.s32 q, %2, %3;\n\t@q ld.shared.b64 %0, [%1];\n\t}\n"
+      : "+l"(v)
+      : "r"(smem_u32addr(p)), "r"(idx), "r"(lim)
       : "memory");
 }
 
@@ -175,8 +191,8 @@ __device__ __forceinline__ void warp_load_bitonic(const KeyT* A, int X, const Ke
 #pragma unroll
   for (int k = 0; k < 32; ++k) {
     KeyT t = key_pad<KeyT>();
-    lds_pred(t, pa + 32 * k, 32 * k < xa);
-    lds_pred(t, pb - 32 * k, 32 * k >= xb);
+    lds_if_lt(t, pa + 32 * k, 32 * k, xa);
+    lds_if_ge(t, pb - 32 * k, 32 * k, xb);
     v[k] = t;
   }
 }
@@ -189,10 +205,19 @@ __device__ __forceinline__ int flip_mask(int lane) {
   return (lane & (32 / E - 1)) * E;
 }
 
+// Runs the bitonic merge of the 1024 items in v (striped layout).  The
+// striped -> blocked transpose goes through the block's own output region
+// `out` (16-byte aligned, at least 32 * nr items): row k (items 32k .. 32k+31)
+// is stored with its 16-byte chunks XOR-swizzled by k & 7, which keeps both
+// the scalar row stores and the 16-byte row loads conflict-free without
+// padding.  After the five half-cleaners of stride >= 32 the rows are ordered
+// (every item of row k is <= every item of row k+1), so rows at or above
+// nr = ceil(m / 32) hold only pads (or real all-ones keys, bit-identical to
+// pads) and are neither stored nor loaded.
 template <typename KeyT>
-__device__ __forceinline__ void warp_bitonic_1024(KeyT (&v)[32], KeyT* scr, int lane) {
+__device__ __forceinline__ void warp_bitonic_1024(KeyT (&v)[32], KeyT* out, int nr, int lane) {
   using V = Vec16<KeyT>;
-  constexpr int ROW = Scratch<KeyT>::ROW;
+  constexpr int E = V::E;
   // half-cleaners of stride 512 .. 32: register distance 16 .. 1
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) {
@@ -200,13 +225,20 @@ __device__ __forceinline__ void warp_bitonic_1024(KeyT (&v)[32], KeyT* scr, int 
     for (int k = 0; k < 32; ++k)
       if ((k & s) == 0) cas(v[k], v[k + s]);
   }
-  // striped -> blocked: row k of the scratch holds items 32k .. 32k+31
+  // striped -> blocked: item 32k + lane at word 32k + (lane ^ E*(k & 7))
 #pragma unroll
-  for (int k = 0; k < 32; ++k) scr[ROW * k + lane] = v[k];
+  for (int k = 0; k < 32; ++k)
+    if (k < nr) out[32 * k + (lane ^ (E * (k & 7)))] = v[k];
   __syncwarp();
-  const typename V::T* row = reinterpret_cast<const typename V::T*>(scr + ROW * lane);
+  if (lane < nr) {
+    const typename V::T* row = reinterpret_cast<const typename V::T*>(out + 32 * lane);
+    const int sw = lane & 7;
 #pragma unroll
-  for (int c = 0; c < 32 / V::E; ++c) V::unpack(row[c], &v[c * V::E]);
+    for (int c = 0; c < 32 / E; ++c) V::unpack(row[c ^ sw], &v[c * E]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = key_pad<KeyT>();
+  }
   __syncwarp();
   // half-cleaners of stride 16 .. 1 inside the lane
   const int F = flip_mask<KeyT>(lane);
@@ -234,18 +266,19 @@ __device__ __forceinline__ void sts128(uint32_t addr, const uint64_t* v) {
   asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(addr), "l"(v[0]), "l"(v[1]) : "memory");
 }
 
-__device__ __forceinline__ void sts128_pred(uint32_t addr, const uint32_t* v, bool p) {
+// 16-byte store when a <= b (signed), compare and store in one predicate.
+__device__ __forceinline__ void sts128_if_le(uint32_t addr, const uint32_t* v, int a, int b) {
   asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t@q st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n\t}\n" ::"r"(
+      "{\n\t.reg .pred q;\n\tsetp.le.s32 q, %5, %6;\n\t@q st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n\t}\n" ::"r"(
           addr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"((int)p)
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(a), "r"(b)
       : "memory");
 }
-__device__ __forceinline__ void sts128_pred(uint32_t addr, const uint64_t* v, bool p) {
+__device__ __forceinline__ void sts128_if_le(uint32_t addr, const uint64_t* v, int a, int b) {
   asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t@q st.shared.v2.b64 [%0], {%1, %2};\n\t}\n" ::"r"(
+      "{\n\t.reg .pred q;\n\tsetp.le.s32 q, %3, %4;\n\t@q st.shared.v2.b64 [%0], {%1, %2};\n\t}\n" ::"r"(
           addr),
-      "l"(v[0]), "l"(v[1]), "r"((int)p)
+      "l"(v[0]), "l"(v[1]), "r"(a), "r"(b)
       : "memory");
 }
 
@@ -270,7 +303,7 @@ __device__ __forceinline__ void warp_store_block(KeyT* out, int m, KeyT (&v)[32]
 #pragma unroll
   for (int c = 0; c < 32 / E; ++c) {
     const int pos = (c * E) ^ F;                      // item offset of the chunk in the row
-    sts128_pred(row + (uint32_t)(pos * SZ), &v[c * E], pos + E <= room);
+    sts128_if_le(row + (uint32_t)(pos * SZ), &v[c * E], pos + E, room);
   }
   if (m < kBlockItems && (m % E) != 0) {
 #pragma unroll
@@ -284,12 +317,14 @@ __device__ __forceinline__ void warp_store_block(KeyT* out, int m, KeyT (&v)[32]
   }
 }
 
+// `out` is 16-byte aligned; the warp may use out[0, 32 * ceil((X + Y) / 32))
+// as transpose space, so up to 31 items past the block's end must be free.
 template <typename KeyT>
 __device__ __forceinline__ void warp_merge_block(const KeyT* A, int X, const KeyT* B, int Y,
-                                                 KeyT* out, KeyT* scr, int lane, bool xout) {
+                                                 KeyT* out, int lane, bool xout) {
   KeyT v[32];
   warp_load_bitonic(A, X, B, Y, v, lane);
-  warp_bitonic_1024(v, scr, lane);
+  warp_bitonic_1024(v, out, (X + Y + 31) >> 5, lane);
   warp_store_block<KeyT>(out, X + Y, v, lane, xout);
 }
 
@@ -303,8 +338,8 @@ __device__ __forceinline__ void warp_merge_block(const KeyT* A, int X, const Key
 // ---------------------------------------------------------------------------
 template <typename KeyT>
 __device__ __forceinline__ void cta_merge_level(const KeyT* src, KeyT* dst, int my_off, int my_len,
-                                                int nseq, KeyT* scr, int warp, int nwarps,
-                                                int lane, bool xout) {
+                                                int nseq, int warp, int nwarps, int lane,
+                                                bool xout) {
   constexpr int E = Vec16<KeyT>::E;
   int item = 0;
   int outoff = 0;
@@ -322,7 +357,7 @@ __device__ __forceinline__ void cta_merge_level(const KeyT* src, KeyT* dst, int 
       const int a0 = warp_corank(A, a_len, B, b_len, d0, lane);
       const int a1 = (d0 + m == L) ? a_len : warp_corank(A, a_len, B, b_len, d0 + m, lane);
       const int X = a1 - a0;
-      warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outoff + d0, scr, lane, xout);
+      warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outoff + d0, lane, xout);
     }
     outoff += (L + E - 1) / E * E;
   }
@@ -398,14 +433,16 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 }
 
 // Bulk copy of `bytes` (multiple of 16, 16-byte aligned) from this CTA's
-// shared memory to global memory; waits until the copy has completed.
+// shared memory to global memory; waits until the copy has read its source,
+// after which the shared memory may be reused or released (the global writes
+// complete on their own, before the grid completes).
 __device__ __forceinline__ void bulk_s2g_and_wait(void* dst_gmem, const void* src_smem,
                                                   unsigned bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
                "r"(smem_u32addr(src_smem)), "r"(bytes)
                : "memory");
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 __device__ __forceinline__ void set_device_error(int* err, int code) {

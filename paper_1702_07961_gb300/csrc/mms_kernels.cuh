@@ -2,8 +2,8 @@
 // their tile geometry.  A tile is S = 1024 * tile_warps items; the base case
 // sorts tiles of S keys and every merge round writes output tiles of S keys.
 // Defaults: 8 warps (8192 keys) for 4-byte keys, 4 warps (4096 keys) for
-// 8-byte keys, so that two CTAs' shared memory (two tile buffers plus the
-// per-warp transpose scratch) fit in one SM.
+// 8-byte keys, so that three CTAs' shared memory (two tile buffers each) fit
+// in one SM.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -18,12 +18,17 @@ constexpr int kDevOk = 0;
 constexpr int kDevErrTimeout = 1;       // an mbarrier wait ran out of its bound
 constexpr int kDevErrInternal = 2;      // a consistency check failed
 
-// CTAs per SM the kernels are compiled for (register budget): 16 resident
-// warps for 4-byte keys, 8 for 8-byte keys.
+// CTAs per SM the tile kernels are compiled for (register budget): three
+// CTAs of 8 warps (4-byte keys) or of 4 warps (8-byte keys), whose shared
+// memory (two tile buffers each, about 66 KB) fits three to an SM.
 template <typename KeyT, int WARPS>
 struct MinBlocks {
-  static constexpr int value = (sizeof(KeyT) == 4 ? 16 : 8) / WARPS > 0 ? (sizeof(KeyT) == 4 ? 16 : 8) / WARPS : 1;
+  static constexpr int value = 3;
 };
+
+// Items of slack past a tile buffer: a partial block's transpose may use up
+// to 31 items past the block's end.
+constexpr int kTileSlack = 32;
 
 inline int default_tile_warps(int key_bytes) { return key_bytes == 8 ? 4 : 8; }
 inline bool valid_tile_warps(int key_bytes, int w) {
@@ -31,7 +36,7 @@ inline bool valid_tile_warps(int key_bytes, int w) {
 }
 
 size_t tile_sort_smem_bytes(int key_bytes, int warps);
-size_t merge_pass_smem_bytes(int key_bytes, int warps);
+size_t merge_pass_smem_bytes(int key_bytes, int warps, int K);
 
 // Base case: sorts every tile of 1024 * tile_warps keys; in == out allowed.
 // xin / xout: apply the float order transform on load / its inverse on store.

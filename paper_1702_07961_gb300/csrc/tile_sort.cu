@@ -52,8 +52,8 @@ __device__ __forceinline__ void warp_sort_1024(KeyT (&v)[32], int lane) {
       const KeyT a = v[r], b = v[31 - r];
       const KeyT pa = shfl_xor(b, mask);   // partner's register 31-r pairs with my r
       const KeyT pb = shfl_xor(a, mask);   // partner's register r pairs with my 31-r
-      v[r] = upper ? (a > pa ? a : pa) : (a < pa ? a : pa);
-      v[31 - r] = upper ? (b > pb ? b : pb) : (b < pb ? b : pb);
+      v[r] = upper ? kmax(a, pa) : kmin(a, pa);
+      v[31 - r] = upper ? kmax(b, pb) : kmin(b, pb);
     }
 #pragma unroll
     for (int ls = (1 << lg) >> 2; ls >= 1; ls >>= 1) {
@@ -61,7 +61,7 @@ __device__ __forceinline__ void warp_sort_1024(KeyT (&v)[32], int lane) {
 #pragma unroll
       for (int r = 0; r < 32; ++r) {
         const KeyT p = shfl_xor(v[r], ls);
-        v[r] = up ? (v[r] > p ? v[r] : p) : (v[r] < p ? v[r] : p);
+        v[r] = up ? kmax(v[r], p) : kmin(v[r], p);
       }
     }
 #pragma unroll
@@ -104,9 +104,8 @@ __device__ __forceinline__ void tile_sort_finish(KeyT (&v)[32], KeyT* out, long 
                                                  long long base, unsigned char* smem_raw) {
   constexpr int T = WARPS * kBlockItems;
   KeyT* bufX = reinterpret_cast<KeyT*>(smem_raw);
-  KeyT* bufY = bufX + T;
+  KeyT* bufY = bufX + T + kTileSlack;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  KeyT* scr = bufY + T + warp * Scratch<KeyT>::ITEMS;
 
   warp_sort_1024(v, lane);
   const long long trem = n - base;
@@ -130,8 +129,7 @@ __device__ __forceinline__ void tile_sort_finish(KeyT (&v)[32], KeyT* out, long 
   KeyT* dst = bufY;
   int nseq = WARPS;
   while (nseq > 1) {
-    cta_merge_level<KeyT>(src, dst, my_off, my_len, nseq, scr, warp, WARPS, lane,
-                          XOUT && nseq <= 2);
+    cta_merge_level<KeyT>(src, dst, my_off, my_len, nseq, warp, WARPS, lane, XOUT && nseq <= 2);
     next_seq<KeyT>(my_off, my_len, nseq, lane);
     nseq = (nseq + 1) >> 1;
     __syncthreads();
@@ -225,9 +223,10 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<uint64_t, WARPS>::value
   tile_sort_finish<uint64_t, WARPS, false>(v, out, n, base, smem_raw);
 }
 
+// Two tile buffers, each with room for a partial block's transpose past the
+// tile's end (the last, partial tile of an array).
 size_t tile_sort_smem_bytes(int key_bytes, int warps) {
-  const size_t scratch = key_bytes == 8 ? Scratch<uint64_t>::ITEMS : Scratch<uint32_t>::ITEMS;
-  return (size_t)key_bytes * (2 * warps * kBlockItems + warps * scratch);
+  return (size_t)key_bytes * 2 * (warps * kBlockItems + kTileSlack);
 }
 
 template <typename KeyT, int WARPS, bool XIN, bool XOUT>
