@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + sizeof(KeyT) * 2 * (size_t)cap);
 
   const long long t = blockIdx.x;
-  const long long g = t / tpg, j = t % tpg;
+  const unsigned tq = (unsigned)blockIdx.x / (unsigned)tpg;    // tiles and tpg fit in 32 bits
+  const long long g = tq, j = (long long)((unsigned)blockIdx.x - tq * (unsigned)tpg);
   const long long gstart = g * run_len * K;
   const long long grest = n - gstart;
   const long long gsize = grest < run_len * K ? grest : run_len * K;
@@ -193,7 +194,10 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
   }
   c_first -= c_nb;
 
-  const bool ok = mbar_wait_bounded(bar, 0);
+  // One thread polls the staging barrier; the others wait at the CTA barrier
+  // (no issue slots spent polling), which also orders the staged data and the
+  // ragged-end stores before every warp's reads.
+  const bool ok = (threadIdx.x == 0) ? mbar_wait_bounded(bar, 0) : true;
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) set_device_error(dev_err, kDevErrTimeout);
     return;
@@ -251,7 +255,8 @@ static cudaError_t launch_merge_t(const void* in, void* out, long long n, long l
   if (e != cudaSuccess) return e;
   const long long S = (long long)WARPS * kBlockItems;
   const long long ntiles = num_tiles(S, n, run_len, K);
-  const long long tpg = run_len * K / S;
+  long long tpg = run_len * K / S;
+  if (tpg > 0xFFFFFFFFll) tpg = 0xFFFFFFFFll;   // more than the grid: every tile is in group 0
   k<<<(unsigned)ntiles, WARPS * 32, smem, s>>>(static_cast<const KeyT*>(in), static_cast<KeyT*>(out),
                                               n, run_len, K, table, tpg, dev_err);
   return cudaGetLastError();

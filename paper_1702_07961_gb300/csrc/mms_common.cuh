@@ -397,18 +397,19 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned by
                : "memory");
 }
 
-// Waits for phase `parity` of the barrier, giving up after roughly two
-// seconds of polling; returns false on time-out.
+// Waits for phase `parity` of the barrier (each try_wait may suspend the
+// thread for up to 100 us), giving up after roughly two seconds; returns
+// false on time-out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
   const uint32_t addr = smem_u32addr(bar);
   const long long t0 = clock64();
   for (long long it = 0; it < (1ll << 26); ++it) {
     uint32_t done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(addr), "r"(parity)
+        : "r"(addr), "r"(parity), "r"(100000u)
         : "memory");
     if (done) return true;
     if (clock64() - t0 > 4000000000ll) break;
