@@ -133,6 +133,66 @@ mms_status mms_merge_pass(mms_key_type kt, const void* d_in, void* d_out, size_t
                           size_t run_len, int K, const int64_t* d_table, void* d_ws,
                           size_t ws_bytes, void* stream);
 
+/* ---- batched (segmented) sorting ------------------------------------------- */
+
+/* Many independent arrays ("segments") of uneven size, back to back in one
+ * buffer, each sorted on its own (ascending, stable) by the same method as a
+ * whole array: a base case, then K-way merge rounds (Sec. 4).  The paper
+ * sorts one array; batching is this library's extension.  Segment s is
+ * d_keys[d_offsets[s], d_offsets[s + 1]); d_offsets (device, 8-byte aligned)
+ * holds num_segments + 1 non-decreasing entries from 0 to total_n.  Every
+ * segment gets the fanout K of its size class ceil(log2 n) and its own number
+ * of rounds; the whole launch sequence needs no host synchronisation, so it
+ * can be captured into a CUDA graph (mms_segmented_graph_create).  Offsets
+ * out of order, or a segment above max_segment_items, set the workspace
+ * status word to MMS_ERR_INTERNAL (read it with mms_workspace_status). */
+typedef struct {
+  int class_fanout[33];       /* K (2..32) for segments of size class c = ceil(log2 n); 0 =
+                                 default (4 for 4-byte keys, 8 for 8-byte keys and key-value
+                                 batches).  Filled by the package's autotuner. */
+  size_t max_segment_items;   /* largest segment (bounds the rounds launched); 0 = total_n */
+  int tile_items;             /* 0 = mms_tile_items (key-value batches: 4096); else as for
+                                 mms_options.tile_items */
+  int num_events;             /* events[0] before the first kernel, events[1] after the
+                                 planning kernels (and the value copy), events[2] after the
+                                 base case, events[3 + r] after merge round r, the last after
+                                 the value gather (key-value batches) */
+  void** events;
+  int reserved[4];
+} mms_segmented_options;
+
+/* Workspace bytes of a batch: one ping-pong copy of the keys (two 8-byte
+ * composite buffers and a copy of the values for key-value batches), the
+ * per-segment plan, the tile descriptors of every phase, the pivot table of
+ * one round, and the status word. */
+size_t mms_segmented_workspace_bytes(mms_key_type kt, size_t total_n, size_t num_segments,
+                                     int with_values, const mms_segmented_options* opt);
+
+/* Merge rounds a batch launches (segments that need fewer skip the rest). */
+int mms_segmented_rounds(mms_key_type kt, size_t max_segment_items, int with_values,
+                         const mms_segmented_options* opt);
+
+/* Sorts every segment of d_keys in place; with d_values (4-byte keys only,
+ * total_n < 2^32) the 32-bit values move with their keys.  d_ws (256-byte
+ * aligned, mms_segmented_workspace_bytes) is required.  Asynchronous on
+ * `stream`. */
+mms_status mms_segmented_sort(mms_key_type kt, void* d_keys, uint32_t* d_values,
+                              const uint64_t* d_offsets, size_t num_segments, size_t total_n,
+                              void* d_ws, size_t ws_bytes, void* stream,
+                              const mms_segmented_options* opt);
+
+/* A batched sort captured once into a CUDA graph and replayed with one
+ * launch per call: the same buffers, offsets and workspace every time (their
+ * contents may change between launches).  Creation queues no work; the
+ * options' events are ignored. */
+typedef struct mms_graph_s* mms_graph;
+mms_status mms_segmented_graph_create(mms_key_type kt, void* d_keys, uint32_t* d_values,
+                                      const uint64_t* d_offsets, size_t num_segments,
+                                      size_t total_n, void* d_ws, size_t ws_bytes,
+                                      const mms_segmented_options* opt, mms_graph* out);
+mms_status mms_graph_launch(mms_graph g, void* stream);
+void mms_graph_destroy(mms_graph g);
+
 /* ---- sorting without allocating -------------------------------------------- */
 
 /* No counterpart in the paper: a convenience for callers that cannot allocate

@@ -192,3 +192,20 @@ def merge_pass(data: np.ndarray, run_len: int, K: int, values: np.ndarray | None
         if v is not None:
             v[gs:ge] = vs
     return k, v
+
+
+def segmented_sort(keys: np.ndarray, offsets, values: np.ndarray | None = None):
+    """Batched sort: every segment keys[offsets[s]:offsets[s+1]] sorted on its
+    own, stably (values move with their keys) -- the definition of sorting many
+    independent arrays, applied one array at a time."""
+    k = np.array(keys, copy=True)
+    v = None if values is None else np.array(values, dtype=np.uint32, copy=True)
+    off = np.asarray(offsets, dtype=np.int64)
+    for s in range(off.shape[0] - 1):
+        a, b = int(off[s]), int(off[s + 1])
+        if b - a > 1:
+            ks, vs = sort(k[a:b], None if v is None else v[a:b])
+            k[a:b] = ks
+            if v is not None:
+                v[a:b] = vs
+    return k, v

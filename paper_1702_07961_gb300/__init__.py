@@ -18,7 +18,8 @@ import threading
 
 __all__ = ["load", "KEY_U32", "KEY_U64", "KEY_F32", "key_type_of", "sort_keys", "sort_pairs",
            "workspace_bytes", "tile_items", "plan", "tile_sort", "splitter_rows", "splitter",
-           "merge_pass", "workspace_status", "MMSError", "sort_keys_noalloc", "NOALLOC_MAX_KEYS"]
+           "merge_pass", "workspace_status", "MMSError", "sort_keys_noalloc", "NOALLOC_MAX_KEYS",
+           "segmented_workspace_bytes", "segmented_rounds", "segmented_sort", "SegmentedGraph"]
 
 KEY_U32, KEY_U64, KEY_F32 = 0, 1, 2
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -39,6 +40,12 @@ class _Options(ctypes.Structure):
     _fields_ = [("fanout", ctypes.c_int), ("num_events", ctypes.c_int),
                 ("events", ctypes.POINTER(ctypes.c_void_p)), ("tile_items", ctypes.c_int),
                 ("reserved", ctypes.c_int * 3)]
+
+
+class _SegOptions(ctypes.Structure):
+    _fields_ = [("class_fanout", ctypes.c_int * 33), ("max_segment_items", ctypes.c_size_t),
+                ("tile_items", ctypes.c_int), ("num_events", ctypes.c_int),
+                ("events", ctypes.POINTER(ctypes.c_void_p)), ("reserved", ctypes.c_int * 4)]
 
 
 def load() -> ctypes.CDLL:
@@ -78,6 +85,19 @@ def load() -> ctypes.CDLL:
         L.mms_merge_pass.restype = i32
         L.mms_sort_keys_noalloc.argtypes = [i32, vp, sz, vp]
         L.mms_sort_keys_noalloc.restype = i32
+        L.mms_segmented_workspace_bytes.argtypes = [i32, sz, sz, i32, ctypes.POINTER(_SegOptions)]
+        L.mms_segmented_workspace_bytes.restype = sz
+        L.mms_segmented_rounds.argtypes = [i32, sz, i32, ctypes.POINTER(_SegOptions)]
+        L.mms_segmented_rounds.restype = i32
+        L.mms_segmented_sort.argtypes = [i32, vp, vp, vp, sz, sz, vp, sz, vp, ctypes.POINTER(_SegOptions)]
+        L.mms_segmented_sort.restype = i32
+        L.mms_segmented_graph_create.argtypes = [i32, vp, vp, vp, sz, sz, vp, sz,
+                                                 ctypes.POINTER(_SegOptions), ctypes.POINTER(vp)]
+        L.mms_segmented_graph_create.restype = i32
+        L.mms_graph_launch.argtypes = [vp, vp]
+        L.mms_graph_launch.restype = i32
+        L.mms_graph_destroy.argtypes = [vp]
+        L.mms_graph_destroy.restype = None
         L.mms_status_string.argtypes = [i32]
         L.mms_status_string.restype = ctypes.c_char_p
         L.mms_last_error_detail.argtypes = [ctypes.c_char_p, sz]
@@ -236,3 +256,102 @@ def sort_keys_noalloc(keys, stream=None, kt: int | None = None):
     if status != 0:
         raise MMSError(status, f"mms_sort_keys_noalloc failed: {load().mms_status_string(status).decode()}")
     return keys
+
+
+# ---- batched (segmented) sorting ------------------------------------------------------
+
+def _seg_opts(class_fanout=None, max_segment_items: int = 0, tile_items: int = 0, events=None,
+              stream=None):
+    o = _SegOptions()
+    if class_fanout:
+        items = class_fanout.items() if isinstance(class_fanout, dict) else enumerate(class_fanout)
+        for c, k in items:
+            o.class_fanout[int(c)] = int(k)
+    o.max_segment_items = int(max_segment_items)
+    o.tile_items = int(tile_items)
+    if events:
+        for e in events:
+            if not e.cuda_event:
+                e.record(stream)
+        arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
+        o.num_events = len(events)
+        o.events = ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
+        o._keep = arr
+    return o
+
+
+def segmented_workspace_bytes(kt: int, total_n: int, num_segments: int, with_values: bool = False,
+                              class_fanout=None, max_segment_items: int = 0, tile_items: int = 0) -> int:
+    o = _seg_opts(class_fanout, max_segment_items, tile_items)
+    return int(load().mms_segmented_workspace_bytes(kt, total_n, num_segments, int(with_values),
+                                                    ctypes.byref(o)))
+
+
+def segmented_rounds(kt: int, max_segment_items: int, with_values: bool = False, class_fanout=None,
+                     tile_items: int = 0) -> int:
+    o = _seg_opts(class_fanout, 0, tile_items)
+    return int(load().mms_segmented_rounds(kt, max_segment_items, int(with_values), ctypes.byref(o)))
+
+
+def segmented_sort(keys, offsets, values=None, workspace=None, stream=None, kt: int | None = None,
+                   class_fanout=None, max_segment_items: int = 0, tile_items: int = 0, events=None):
+    """Sorts every segment keys[offsets[s]:offsets[s+1]] in place (one batched call).
+
+    ``offsets``: int64 CUDA tensor of num_segments + 1 entries from 0 to keys.numel().
+    ``values``: optional 32-bit values that move with 4-byte keys.
+    ``class_fanout``: fanout K per size class ceil(log2 n) (dict or list), e.g. from
+    :mod:`paper_1702_07961_gb300.autotune`.
+    """
+    import torch
+    assert keys.is_cuda and keys.is_contiguous() and offsets.is_cuda and offsets.is_contiguous()
+    assert offsets.dtype == torch.int64
+    kt = key_type_of(keys) if kt is None else kt
+    nseg = offsets.numel() - 1
+    total = keys.numel()
+    if workspace is None:
+        workspace = torch.empty(segmented_workspace_bytes(kt, total, nseg, values is not None, class_fanout,
+                                                          max_segment_items, tile_items),
+                                dtype=torch.uint8, device=keys.device)
+    o = _seg_opts(class_fanout, max_segment_items, tile_items, events, stream)
+    _check(load().mms_segmented_sort(kt, _ptr(keys), _ptr(values), _ptr(offsets), nseg, total,
+                                     _ptr(workspace), workspace.numel(), _stream_handle(stream),
+                                     ctypes.byref(o)))
+    return keys, values
+
+
+class SegmentedGraph:
+    """One batched sort captured into a CUDA graph: ``launch()`` replays it on the
+    same buffers (whose contents may change between launches) with one graph launch."""
+
+    def __init__(self, keys, offsets, values=None, workspace=None, kt: int | None = None,
+                 class_fanout=None, max_segment_items: int = 0, tile_items: int = 0):
+        import torch
+        kt = key_type_of(keys) if kt is None else kt
+        nseg = offsets.numel() - 1
+        total = keys.numel()
+        if workspace is None:
+            workspace = torch.empty(segmented_workspace_bytes(kt, total, nseg, values is not None, class_fanout,
+                                                              max_segment_items, tile_items),
+                                    dtype=torch.uint8, device=keys.device)
+        self._keep = (keys, offsets, values, workspace)
+        self.workspace = workspace
+        o = _seg_opts(class_fanout, max_segment_items, tile_items)
+        h = ctypes.c_void_p()
+        _check(load().mms_segmented_graph_create(kt, _ptr(keys), _ptr(values), _ptr(offsets), nseg, total,
+                                                 _ptr(workspace), workspace.numel(), ctypes.byref(o),
+                                                 ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(load().mms_graph_launch(self._h, _stream_handle(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mms_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -93,6 +93,10 @@ mms_status check_launch(cudaError_t e, const char* where) {
 
 }  // namespace
 
+namespace mms {
+void set_error_detail(const char* msg) { snprintf(g_detail, sizeof g_detail, "%s", msg); }
+}  // namespace mms
+
 extern "C" {
 
 const char* mms_status_string(mms_status s) {

@@ -1,58 +1,11 @@
-// merge_pass.cu -- one K-way merge round of GPU Multiway Mergesort (Sec. 4.2
-// "I/O Efficient Merging", Sec. 5.1 I/O analysis).
-//
-// One CTA produces one output tile of S = 1024 * WARPS items of its group of K
-// runs.  The splitter table gives, for the tile's start and end, the pivot in
-// every run (Sec. 4.1), so the tile's inputs are K contiguous segments whose
-// lengths sum to S.  The CTA:
-//   1. stages the K segments into shared memory with 1-D TMA bulk copies
-//      (cp.async.bulk, one mbarrier; the < 16-byte ragged ends of each
-//      segment by plain loads), so every input byte is read from HBM once;
-//   2. merges them along a binary merge tree of ceil(log2 K) levels (the
-//      paper's minBlockHeap has the same levels), one level at a time: every
-//      tree node of the level (a pair of sequences) is cut into 1024-item
-//      output blocks, the blocks of the level are dealt to the warps, and a
-//      CTA barrier separates the levels.  A node's output is written into the
-//      span its segments were staged in, alternating between two buffers by
-//      level; every segment span carries 32 items of slack so that a node's
-//      last, partial block can use its output region as transpose space.
-//      Each block is merged by the conflict-free warp bitonic block merge;
-//   3. writes the tile with one TMA bulk store, so every output byte is
-//      written once: 2 * S * sizeof(key) bytes of HBM traffic per tile.
-#include "mms_common.cuh"
-#include "mms_kernels.cuh"
+// merge_pass.cu -- one K-way merge round over a whole array: one CTA per
+// output tile, running the CTA body of merge_tile.cuh.
+#include "merge_tile.cuh"
 
 namespace mms {
 
-// Shared-memory geometry of a merge CTA for fanout K.  X: the staged
-// segments, each at a 16-byte aligned span start R_r (up to 2E-2 items of
-// alignment slack and 32 items of transpose slack per segment), and the odd
-// tree levels' inputs; Y: the same spans, one buffer per level parity.
-template <typename KeyT, int WARPS>
-struct MergeGeom {
-  static constexpr int E = Vec16<KeyT>::E;
-  static constexpr int S = WARPS * kBlockItems;
-  static constexpr int kSlack = 32;
-  __host__ __device__ static constexpr int cap(int K) { return S + K * (2 * E + kSlack) + E; }
-  // control block: mbarrier (8), error flag (4), pad (4)
-  __host__ __device__ static constexpr size_t bytes(int K) {
-    return sizeof(KeyT) * 2 * (size_t)cap(K) + 16;
-  }
-};
-
 size_t merge_pass_smem_bytes(int key_bytes, int warps, int K) {
-  if (key_bytes == 4) {
-    switch (warps) {
-      case 4: return MergeGeom<uint32_t, 4>::bytes(K);
-      case 8: return MergeGeom<uint32_t, 8>::bytes(K);
-    }
-  } else {
-    switch (warps) {
-      case 2: return MergeGeom<uint64_t, 2>::bytes(K);
-      case 4: return MergeGeom<uint64_t, 4>::bytes(K);
-    }
-  }
-  return 0;
+  return merge_pass_smem_bytes_impl(key_bytes, warps, K);
 }
 
 template <typename KeyT, int WARPS, bool XOUT>
@@ -60,190 +13,15 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
     merge_pass_kernel(const KeyT* __restrict__ in, KeyT* __restrict__ out, long long n,
                       long long run_len, int K, const long long* __restrict__ table,
                       long long tpg, int* dev_err) {
-  using G = MergeGeom<KeyT, WARPS>;
-  constexpr int E = G::E;
-  constexpr int S = G::S;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  const int cap = G::cap(K);
-  KeyT* bufX = reinterpret_cast<KeyT*>(smem_raw);
-  KeyT* bufY = bufX + cap;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cap = MergeGeom<KeyT, WARPS>::cap(K);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + sizeof(KeyT) * 2 * (size_t)cap);
-
   const long long t = blockIdx.x;
   const unsigned tq = (unsigned)blockIdx.x / (unsigned)tpg;    // tiles and tpg fit in 32 bits
   const long long g = tq, j = (long long)((unsigned)blockIdx.x - tq * (unsigned)tpg);
-  const long long gstart = g * run_len * K;
-  const long long grest = n - gstart;
-  const long long gsize = grest < run_len * K ? grest : run_len * K;
-  const long long tiles_here = (gsize + S - 1) / S;
-
-  // Segment of run `lane` for this tile (every warp computes the same).
-  const bool act = lane < K;
-  const long long rstart = gstart + (long long)lane * run_len;
-  long long rlen = n - rstart;
-  rlen = rlen < 0 ? 0 : (rlen > run_len ? run_len : rlen);
-  long long lo = 0, hi = 0;
-  if (act) {
-    lo = (j == 0) ? 0 : table[t * K + lane];
-    hi = (j + 1 < tiles_here) ? table[(t + 1) * K + lane] : rlen;
-  }
-  // The pivot rows must describe segments inside their runs whose lengths sum
-  // to this tile's size; anything else would overrun the staging buffer.
-  const long long want = (gsize - j * S) < S ? (gsize - j * S) : S;
-  {
-    const bool bad_seg = act && (lo < 0 || hi < lo || hi > rlen);
-    long long sum = act ? hi - lo : 0;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (__any_sync(0xffffffffu, bad_seg) || sum != want || K > kMaxFanout || K < 2 ||
-        (smem_u32addr(smem_raw) & 1023u) != 0) {
-      if (threadIdx.x == 0) set_device_error(dev_err, kDevErrInternal);
-      return;                                          // uniform over the CTA
-    }
-  }
-  const long long gsrc = rstart + lo;                  // first item, global index
-  const int len = act ? (int)(hi - lo) : 0;
-  const int head = act ? (int)(gsrc % E) : 0;          // items copied before the segment
-  const int span = (head + len + E - 1) / E * E + G::kSlack;   // staged span + transpose slack
-  int incl = span;
-  int lincl = len;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int x = __shfl_up_sync(0xffffffffu, incl, o);
-    const int y = __shfl_up_sync(0xffffffffu, lincl, o);
-    if (lane >= o) {
-      incl += x;
-      lincl += y;
-    }
-  }
-  const int R = incl - span;                           // span start of segment `lane`
-  const int lpre = lincl - len;                        // items in segments before `lane`
-  // Bulk part: [gsrc - head, floor_E(gsrc + len)); the rest by plain loads.
-  const long long bulk_lo = gsrc - head;
-  const long long bulk_hi = (gsrc + len) / E * E;
-  const unsigned bulk_bytes =
-      (act && bulk_hi > bulk_lo) ? (unsigned)((bulk_hi - bulk_lo) * sizeof(KeyT)) : 0u;
-
   if (threadIdx.x == 0) mbar_init(bar, 1);
-  __syncthreads();
-  if (warp == 0) {
-    unsigned total = bulk_bytes;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
-    if (lane == 0) mbar_arrive_expect_tx(bar, total);
-    __syncwarp();
-    if (bulk_bytes) bulk_g2s(bufX + R, in + bulk_lo, bulk_bytes, bar);
-  } else if (warp == 1) {
-    // Ragged ends, one segment at a time, consecutive lanes -> consecutive words.
-    for (int r = 0; r < K; ++r) {
-      const long long s_src = __shfl_sync(0xffffffffu, gsrc, r);
-      const int s_len = __shfl_sync(0xffffffffu, len, r);
-      const int s_off = __shfl_sync(0xffffffffu, R + head, r);
-      const long long s_bhi = __shfl_sync(0xffffffffu, bulk_hi, r);
-      const long long s_blo = __shfl_sync(0xffffffffu, bulk_lo, r);
-      const long long from = (s_bhi > s_blo) ? s_bhi : s_src;   // first item not bulk-copied
-      const long long e = from + lane;
-      if (e < s_src + s_len) bufX[s_off + (int)(e - s_src)] = in[e];
-    }
-  }
-
-  // Merge-tree nodes, one per lane, in level order: node (level l >= 1, pair q)
-  // merges child A = segments [q*2^l, q*2^l + 2^(l-1)) and child B = the rest
-  // of [q*2^l, (q+1)*2^l) (clipped to K).  Every warp derives the same table.
-  int nl = 0, nnodes = 0, c_level = 0, c_pair = 0;
-  {
-    int cnt = K, idx = 0;
-    for (int l = 1; cnt > 1; ++l) {
-      const int pairs = (cnt + 1) >> 1;
-      if (lane >= idx && lane < idx + pairs) {
-        c_level = l;
-        c_pair = lane - idx;
-      }
-      idx += pairs;
-      cnt = pairs;
-      nl = l;
-    }
-    nnodes = idx;
-  }
-  const bool is_node = lane < nnodes;
-  const int first = c_pair << c_level;                  // first segment of the node
-  const int mid = first + (1 << (c_level > 0 ? c_level - 1 : 0));
-  const int last = first + (1 << c_level);
-  auto seg_pre = [&](int s) {                           // items in segments [0, s)
-    const int ss = s < K ? s : K;
-    const int v = __shfl_sync(0xffffffffu, lpre, ss & 31);
-    return ss >= K ? (int)want : v;
-  };
-  const int pf = seg_pre(first), pm = seg_pre(mid), pl = seg_pre(last);
-  const int rf = __shfl_sync(0xffffffffu, R, first & 31);
-  const int hf = __shfl_sync(0xffffffffu, head, first & 31);
-  const int rm = __shfl_sync(0xffffffffu, R, mid & 31);
-  const int hm = __shfl_sync(0xffffffffu, head, mid & 31);
-  const int c_lenA = is_node ? pm - pf : 0;
-  const int c_lenB = is_node ? pl - pm : 0;
-  const int c_offA = (c_level == 1) ? rf + hf : rf;     // staged segment vs. child output
-  const int c_offB = (mid < K) ? ((c_level == 1) ? rm + hm : rm) : 0;
-  const int c_out = rf;
-  const int c_nb = (c_lenA + c_lenB + kBlockItems - 1) / kBlockItems;
-  int c_first = c_nb;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int x = __shfl_up_sync(0xffffffffu, c_first, o);
-    if (lane >= o) c_first += x;
-  }
-  c_first -= c_nb;
-
-  // One thread polls the staging barrier; the others wait at the CTA barrier
-  // (no issue slots spent polling), which also orders the staged data and the
-  // ragged-end stores before every warp's reads.
-  const bool ok = (threadIdx.x == 0) ? mbar_wait_bounded(bar, 0) : true;
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) set_device_error(dev_err, kDevErrTimeout);
-    return;
-  }
-
-  // Level by level: the blocks of every node of level lv are dealt to the
-  // warps round-robin; a barrier ends the level.
-  for (int lv = 1; lv <= nl; ++lv) {
-    const unsigned lvm = __ballot_sync(0xffffffffu, is_node && c_level == lv);
-    const int n0 = __ffs(lvm) - 1, n1 = 31 - __clz(lvm);
-    const int it0 = __shfl_sync(0xffffffffu, c_first, n0);
-    const int it1 = __shfl_sync(0xffffffffu, c_first + c_nb, n1);
-    const KeyT* src = (lv & 1) ? bufX : bufY;           // level lv reads level lv-1's buffer
-    KeyT* dst = (lv & 1) ? bufY : bufX;
-    for (int item = it0 + warp; item < it1; item += WARPS) {
-      const unsigned sel = __ballot_sync(0xffffffffu, is_node && c_first <= item && c_nb > 0);
-      const int c = 31 - __clz(sel);
-      const int lenA = __shfl_sync(0xffffffffu, c_lenA, c);
-      const int lenB = __shfl_sync(0xffffffffu, c_lenB, c);
-      const int offA = __shfl_sync(0xffffffffu, c_offA, c);
-      const int offB = __shfl_sync(0xffffffffu, c_offB, c);
-      const int outo = __shfl_sync(0xffffffffu, c_out, c);
-      const int fi = __shfl_sync(0xffffffffu, c_first, c);
-      const KeyT* A = src + offA;
-      const KeyT* B = src + offB;
-      const int L = lenA + lenB;
-      const int d0 = (item - fi) * kBlockItems;
-      const int m = (L - d0) < kBlockItems ? (L - d0) : kBlockItems;
-      const int a0 = warp_corank(A, lenA, B, lenB, d0, lane);
-      const int a1 = (d0 + m == L) ? lenA : warp_corank(A, lenA, B, lenB, d0 + m, lane);
-      const int X = a1 - a0;
-      warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, lane,
-                             XOUT && lv == nl);
-      __syncwarp();
-    }
-    __syncthreads();
-  }
-  // The root node's output is the tile, at span start 0 of the last level's buffer.
-  const KeyT* res = (nl & 1) ? bufY : bufX;
-  const int m = (int)want;
-  KeyT* dstg = out + gstart + j * S;
-  const int body = m / E * E;
-  fence_proxy_async_smem();
-  __syncthreads();
-  if (threadIdx.x == 0 && body > 0) bulk_s2g_and_wait(dstg, res, (unsigned)(body * sizeof(KeyT)));
-  for (int i = body + (int)threadIdx.x; i < m; i += blockDim.x) dstg[i] = res[i];
+  merge_tile<KeyT, WARPS>(in, out, n, run_len, K, g, j, table + t * K, table + (t + 1) * K, XOUT,
+                          dev_err, smem_raw, bar, 0u);
 }
 
 template <typename KeyT, int WARPS, bool XOUT>

@@ -63,9 +63,12 @@ cudaError_t launch_merge_pass(int key_bytes, int tile_warps, bool xout, const vo
                               long long n, long long run_len, int K, const long long* table,
                               int* dev_err, cudaStream_t s);
 
+// Records the detail message mms_last_error_detail() returns on this thread.
+void set_error_detail(const char* msg);
+
 // Output tiles of a round: every group of K runs (K * run_len items, the last
 // group possibly short) is cut into tiles of S items.
-inline long long num_tiles(long long S, long long n, long long run_len, int K) {
+__host__ __device__ inline long long num_tiles(long long S, long long n, long long run_len, int K) {
   const long long G = run_len * K;
   const long long full = n / G;
   const long long rest = n - full * G;

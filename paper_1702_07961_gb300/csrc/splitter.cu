@@ -1,182 +1,16 @@
-// splitter.cu -- parallel partitioning of a K-way merge round (Sec. 4.1).
-//
-// For every output tile j of every group of K sorted runs, one warp finds the
-// pivot indices c[r] (r < K): the number of items run r contributes to the
-// group's first j*S outputs under the strict order (key, run, position).  That
-// order makes the pivots unique even with repeated keys (the paper's
-// non-overlap condition, read on the composite key) and equals a stable merge.
-//
-// Search (one lane per run, K <= 32): stride halving on regular samples.  At
-// stride s the warp holds the exact pivots d of the s-sample problem -- the
-// items at positions s-1, 2s-1, ... of every run -- for rank floor(k/s).
-// Halving s adds one candidate per run just above its pivot; the pivots of the
-// s/2-sample problem for rank floor(2k/s) are then the floor(2k/s) smallest of
-// (old selection expanded) + (candidates), found by dropping the largest items
-// from the top with warp arg-max reductions.  At s = 1 the sample problem is
-// the whole problem.  About log2(k) rounds of two independent loads per lane.
-// Positions past a run's end are padding items ordered after every real item
-// (by run, then position).
-#include "mms_common.cuh"
-#include "mms_kernels.cuh"
+// splitter.cu -- the whole-array splitter: one warp per output tile of a
+// merge round, running splitter_row of splitter.cuh.
+#include "splitter.cuh"
 
 namespace mms {
-
-template <typename KeyT>
-struct Item {
-  KeyT key;
-  bool pad;
-};
-
-template <typename KeyT>
-__device__ __forceinline__ Item<KeyT> load_item(const KeyT* run, long long len, long long pos) {
-  Item<KeyT> it;
-  it.pad = pos >= len;
-  it.key = it.pad ? KeyT(0) : run[pos];
-  return it;
-}
-
-// a (run ra) strictly before b (run rb), ra != rb.
-template <typename KeyT>
-__device__ __forceinline__ bool before_cross(const Item<KeyT>& a, int ra, const Item<KeyT>& b,
-                                             int rb) {
-  if (a.pad != b.pad) return b.pad;
-  if (!a.pad && a.key != b.key) return a.key < b.key;
-  return ra < rb;
-}
-
-__device__ __forceinline__ uint32_t warp_max_u32(uint32_t v) {
-  return __reduce_max_sync(0xffffffffu, v);
-}
-__device__ __forceinline__ uint32_t warp_min_u32(uint32_t v) {
-  return __reduce_min_sync(0xffffffffu, v);
-}
-
-// Lanes with `cond` whose key equals the maximum key among them.
-__device__ __forceinline__ unsigned lanes_with_max(bool cond, uint32_t key) {
-  const uint32_t mx = warp_max_u32(cond ? key : 0u);
-  return __ballot_sync(0xffffffffu, cond && key == mx);
-}
-__device__ __forceinline__ unsigned lanes_with_max(bool cond, uint64_t key) {
-  const uint32_t hi = (uint32_t)(key >> 32), lo = (uint32_t)key;
-  const uint32_t mh = warp_max_u32(cond ? hi : 0u);
-  const bool c2 = cond && hi == mh;
-  const uint32_t ml = warp_max_u32(c2 ? lo : 0u);
-  return __ballot_sync(0xffffffffu, c2 && lo == ml);
-}
-__device__ __forceinline__ unsigned lanes_with_min(bool cond, uint32_t key) {
-  const uint32_t mn = warp_min_u32(cond ? key : 0xffffffffu);
-  return __ballot_sync(0xffffffffu, cond && key == mn);
-}
-__device__ __forceinline__ unsigned lanes_with_min(bool cond, uint64_t key) {
-  const uint32_t hi = (uint32_t)(key >> 32), lo = (uint32_t)key;
-  const uint32_t mh = warp_min_u32(cond ? hi : 0xffffffffu);
-  const bool c2 = cond && hi == mh;
-  const uint32_t ml = warp_min_u32(c2 ? lo : 0xffffffffu);
-  return __ballot_sync(0xffffffffu, c2 && lo == ml);
-}
-
-// Lane holding the largest item among lanes with `cond` (runs compare by
-// (pad, key, run)); -1 if none.
-template <typename KeyT>
-__device__ __forceinline__ int warp_argmax(bool cond, const Item<KeyT>& it) {
-  const unsigned any = __ballot_sync(0xffffffffu, cond);
-  if (!any) return -1;
-  const unsigned pads = __ballot_sync(0xffffffffu, cond && it.pad);
-  if (pads) return 31 - __clz(pads);
-  return 31 - __clz(lanes_with_max(cond, it.key));
-}
-
-template <typename KeyT>
-__device__ __forceinline__ int warp_argmin(bool cond, const Item<KeyT>& it) {
-  const unsigned any = __ballot_sync(0xffffffffu, cond);
-  if (!any) return -1;
-  const unsigned reals = __ballot_sync(0xffffffffu, cond && !it.pad);
-  if (!reals) return __ffs(any) - 1;
-  return __ffs(lanes_with_min(cond && !it.pad, it.key)) - 1;
-}
-
-template <typename KeyT>
-__device__ __forceinline__ Item<KeyT> shfl_item(const Item<KeyT>& it, int src) {
-  Item<KeyT> o;
-  o.key = __shfl_sync(0xffffffffu, it.key, src);
-  o.pad = __shfl_sync(0xffffffffu, (int)it.pad, src) != 0;
-  return o;
-}
-
-__device__ __forceinline__ long long warp_sum_ll(long long v) {
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 template <typename KeyT>
 __global__ void __launch_bounds__(128)
     splitter_kernel(const KeyT* __restrict__ in, long long n, long long run_len, int K,
                     long long S, long long tpg, long long ntiles, long long* __restrict__ table) {
-  const int lane = threadIdx.x & 31;
   const long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (t >= ntiles) return;                      // warp-uniform
-  const long long g = t / tpg, j = t % tpg;
-  const bool act = lane < K;
-  const long long rstart = g * run_len * K + (long long)lane * run_len;
-  long long rlen = n - rstart;
-  rlen = rlen < 0 ? 0 : (rlen > run_len ? run_len : rlen);
-  if (!act) rlen = 0;
-  const KeyT* run = in + (act ? rstart : 0);
-  const long long k = j * S;
-
-  long long d = 0;            // selected samples of this run at the current stride
-  Item<KeyT> e{KeyT(0), false};  // the d-th sample (position d*s-1) when d >= 1
-  const int T = 64 - __clzll(k);
-  for (int lev = T; lev >= 1; --lev) {
-    const int sh = lev - 1;                     // s2 = 2^sh
-    const long long kp = k >> sh;
-    const long long dd = 2 * d;
-    Item<KeyT> o = load_item(run, rlen, ((dd + 1) << sh) - 1);
-    Item<KeyT> z{KeyT(0), false};
-    if (d >= 1) z = load_item(run, rlen, ((dd - 1) << sh) - 1);
-    const long long jrem = 2 * warp_sum_ll(act ? d : 0) + K - kp;   // items to drop
-    long long cnt = dd + 1;
-
-    // Candidates above every selected item are dropped first, in one step.
-    const bool hasZ = act && d >= 1;
-    const int mz = warp_argmax(hasZ, e);
-    bool above = act;
-    if (mz >= 0) {
-      const Item<KeyT> zmax = shfl_item(e, mz);
-      above = act && (lane == mz || before_cross(zmax, mz, o, lane));
-    }
-    const unsigned abovem = __ballot_sync(0xffffffffu, above);
-    const long long u = __popc(abovem);
-    long long pops;
-    if (u <= jrem) {
-      if (above) cnt = dd;
-      pops = jrem - u;
-    } else {                                    // keep only the smallest candidate
-      const int mn = warp_argmin(above, o);
-      if (above && lane != mn) cnt = dd;
-      pops = 0;
-    }
-    // Remaining drops one at a time from the largest current top.
-    Item<KeyT> top = (cnt == dd + 1) ? o : e;
-    for (long long p = 0; p < pops; ++p) {
-      const int w = warp_argmax(act && cnt >= 1, top);
-      if (lane == w) {
-        cnt -= 1;
-        if (cnt >= 1) {
-          if (cnt == dd)
-            top = e;
-          else if (cnt == dd - 1)
-            top = z;
-          else
-            top = load_item(run, rlen, (cnt << sh) - 1);
-        }
-      }
-    }
-    d = cnt;
-    e = top;
-  }
-  if (act) table[t * K + lane] = d;
+  splitter_row<KeyT>(in, n, run_len, K, S, t / tpg, t % tpg, table + t * K);
 }
 
 cudaError_t launch_splitter(int key_bytes, long long S, const void* in, long long n,

@@ -1,0 +1,233 @@
+// tile_sort.cuh -- the CTA body of the base case of GPU Multiway Mergesort
+// (Sec. 4.3 "Internal Memory Sort"), shared by the whole-array base case and
+// the segmented (batched) one: a tile of T = 1024 * WARPS consecutive keys is
+// sorted on its own, producing a sorted run the K-way merge rounds start from.
+//
+// The paper's base case is a per-warp shearsort of a 32 x 32 grid, extended
+// by bitonic merges between warps.  Here each lane sorts the 32 keys it loaded
+// with an in-register sorting network, the warp finishes its 1024 keys with
+// register/shuffle bitonic merges (no shared memory, so no bank traffic), and
+// the CTA merges the warps' blocks with the same conflict-free block merge the
+// merge rounds use.  HBM traffic: one coalesced 128-bit read and one coalesced
+// 128-bit write of every key.
+#pragma once
+
+#include "mms_common.cuh"
+#include "mms_kernels.cuh"
+
+namespace mms {
+
+// Bitonic sorting network over a lane's 32 registers (ascending).
+template <typename KeyT>
+__device__ __forceinline__ void lane_sort32(KeyT (&v)[32]) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          if ((i & k) == 0)
+            cas(v[i], v[ixj]);
+          else
+            cas(v[ixj], v[i]);
+        }
+      }
+    }
+  }
+}
+
+// Sorts 1024 keys held as 32 per lane (any assignment) into the blocked
+// layout: after the call register j of lane l holds sorted item
+// 32*l + (j ^ flip_mask(l)), the layout warp_store_block writes out.
+// Level lg merges runs of 2^(lg-1) lanes: a reversed-partner stage across the
+// run pair, lane half-cleaners by shuffle, then in-lane half-cleaners.
+template <typename KeyT>
+__device__ __forceinline__ void warp_sort_1024(KeyT (&v)[32], int lane) {
+  lane_sort32(v);
+#pragma unroll
+  for (int lg = 1; lg <= 5; ++lg) {
+    const int mask = (1 << lg) - 1;
+    const bool upper = (lane & (1 << (lg - 1))) != 0;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const KeyT a = v[r], b = v[31 - r];
+      const KeyT pa = shfl_xor(b, mask);   // partner's register 31-r pairs with my r
+      const KeyT pb = shfl_xor(a, mask);   // partner's register r pairs with my 31-r
+      v[r] = upper ? kmax(a, pa) : kmin(a, pa);
+      v[31 - r] = upper ? kmax(b, pb) : kmin(b, pb);
+    }
+#pragma unroll
+    for (int ls = (1 << lg) >> 2; ls >= 1; ls >>= 1) {
+      const bool up = (lane & ls) != 0;
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        const KeyT p = shfl_xor(v[r], ls);
+        v[r] = up ? kmax(v[r], p) : kmin(v[r], p);
+      }
+    }
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+      const bool f = (lg == 5) && ((flip_mask<KeyT>(lane) & s) != 0);
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if ((k & s) == 0) cas_dir(v[k], v[k + s], f);
+    }
+  }
+}
+
+template <typename KeyT, bool XIN>
+__device__ __forceinline__ KeyT xform_in(KeyT k) {
+  if constexpr (XIN) return (KeyT)f32_to_ordered((uint32_t)k);
+  return k;
+}
+template <typename KeyT, bool XOUT>
+__device__ __forceinline__ KeyT xform_out(KeyT k) {
+  if constexpr (XOUT) return (KeyT)ordered_to_f32((uint32_t)k);
+  return k;
+}
+
+// Writes the sorted tile src[0, m) to global memory: one TMA bulk store of the
+// 16-byte-aligned body, plain stores for the < 16-byte tail.  Every thread
+// must call it (it contains a barrier).
+template <typename KeyT>
+__device__ __forceinline__ void cta_store_tile(const KeyT* src, KeyT* dst, int m) {
+  constexpr int E = 16 / sizeof(KeyT);
+  // A destination off the 16-byte grid (a segment of a batch may start
+  // anywhere) is written with plain coalesced stores.
+  const int body = (((uintptr_t)dst & 15u) == 0) ? m / E * E : 0;
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0 && body > 0) bulk_s2g_and_wait(dst, src, (unsigned)(body * sizeof(KeyT)));
+  for (int i = body + (int)threadIdx.x; i < m; i += blockDim.x) dst[i] = src[i];
+}
+
+// Everything after the load: warp sorts, CTA merge levels, store of the tile.
+template <typename KeyT, int WARPS>
+__device__ __forceinline__ void tile_sort_finish(KeyT (&v)[32], KeyT* out, long long n,
+                                                 long long base, bool xout,
+                                                 unsigned char* smem_raw) {
+  constexpr int T = WARPS * kBlockItems;
+  KeyT* bufX = reinterpret_cast<KeyT*>(smem_raw);
+  KeyT* bufY = bufX + T + kTileSlack;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  warp_sort_1024(v, lane);
+  // The previous tile of a persistent CTA has been read out of shared memory.
+  __syncthreads();
+  const long long trem = n - base;
+  const int m = trem >= T ? T : (int)trem;
+  if constexpr (WARPS == 1) {
+    warp_store_block<KeyT>(bufX, kBlockItems, v, lane, xout);
+    cta_store_tile(bufX, out + base, m);
+    return;
+  }
+  warp_store_block<KeyT>(bufX + warp * kBlockItems, kBlockItems, v, lane, false);
+  __syncthreads();
+
+  // CTA levels: merge the warps' sorted blocks pairwise up to the tile.
+  int my_off = lane * kBlockItems;
+  int my_len = 0;
+  {
+    const long long r2 = n - (base + (long long)lane * kBlockItems);
+    my_len = (lane < WARPS && r2 > 0) ? (r2 >= kBlockItems ? kBlockItems : (int)r2) : 0;
+  }
+  KeyT* src = bufX;
+  KeyT* dst = bufY;
+  int nseq = WARPS;
+  while (nseq > 1) {
+    cta_merge_level<KeyT>(src, dst, my_off, my_len, nseq, warp, WARPS, lane, xout && nseq <= 2);
+    next_seq<KeyT>(my_off, my_len, nseq, lane);
+    nseq = (nseq + 1) >> 1;
+    __syncthreads();
+    KeyT* t = src;
+    src = dst;
+    dst = t;
+  }
+  cta_store_tile(src, out + base, m);
+}
+
+// Sorts the tile of 1024 * WARPS keys of in[0, n) that starts at `base` into
+// the same positions of out (in == out allowed): the CTA body of the base case.
+template <typename KeyT, int WARPS, bool XIN>
+__device__ __forceinline__ void tile_sort_tile(const KeyT* __restrict__ in, KeyT* out, long long n,
+                                               long long base, bool xout,
+                                               unsigned char* smem_raw) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long wbase = base + (long long)warp * kBlockItems;
+  const long long rem = n - wbase;
+  const int cnt = rem <= 0 ? 0 : (rem >= kBlockItems ? kBlockItems : (int)rem);
+
+  using V = Vec16<KeyT>;
+  constexpr int NV = 32 / V::E;          // 16-byte vectors per lane
+  KeyT v[32];
+  if (cnt == kBlockItems && ((uintptr_t)(in + wbase) & 15u) == 0) {
+    const typename V::T* src = reinterpret_cast<const typename V::T*>(in + wbase);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const typename V::T x = __ldg(src + q * 32 + lane);
+      KeyT t[V::E];
+      V::unpack(x, t);
+#pragma unroll
+      for (int c = 0; c < V::E; ++c) v[q * V::E + c] = xform_in<KeyT, XIN>(t[c]);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+#pragma unroll
+      for (int c = 0; c < V::E; ++c) {
+        const int e = q * 32 * V::E + lane * V::E + c;
+        v[q * V::E + c] = e < cnt ? xform_in<KeyT, XIN>(in[wbase + e]) : key_pad<KeyT>();
+      }
+    }
+  }
+  tile_sort_finish<KeyT, WARPS>(v, out, n, base, xout, smem_raw);
+}
+
+// Base case of the key-value sort: 32-bit keys (floats through the order
+// transform when XIN) are read and turned into unique 64-bit composites
+// (ordered key << 32 | pos0 + position in the array), whose ascending order is the
+// stable key order; tiles of composites are then sorted like 64-bit keys.
+template <int WARPS, bool XIN>
+__device__ __forceinline__ void tile_sort_composite_tile(const uint32_t* __restrict__ in,
+                                                         uint64_t* out, long long n,
+                                                         long long base, long long pos0,
+                                                         unsigned char* smem_raw) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long wbase = base + (long long)warp * kBlockItems;
+  const long long rem = n - wbase;
+  const int cnt = rem <= 0 ? 0 : (rem >= kBlockItems ? kBlockItems : (int)rem);
+  uint64_t v[32];
+  if (cnt == kBlockItems && ((uintptr_t)(in + wbase) & 15u) == 0) {
+    const uint4* src = reinterpret_cast<const uint4*>(in + wbase);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint4 x = __ldg(src + q * 32 + lane);
+      const uint32_t k[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint32_t key = XIN ? f32_to_ordered(k[c]) : k[c];
+        const uint64_t pos = (uint64_t)(pos0 + wbase + q * 128 + lane * 4 + c);
+        v[q * 4 + c] = ((uint64_t)key << 32) | pos;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int e = q * 128 + lane * 4 + c;
+        uint64_t x = key_pad<uint64_t>();
+        if (e < cnt) {
+          const uint32_t key = XIN ? f32_to_ordered(in[wbase + e]) : in[wbase + e];
+          x = ((uint64_t)key << 32) | (uint64_t)(pos0 + wbase + e);
+        }
+        v[q * 4 + c] = x;
+      }
+    }
+  }
+  tile_sort_finish<uint64_t, WARPS>(v, out, n, base, false, smem_raw);
+}
+
+}  // namespace mms

@@ -24,7 +24,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["uniform", "permutation", "sortedness", "interleaved", "normal_f32",
-           "index_payload", "make"]
+           "index_payload", "segment_sizes", "offsets_of", "make"]
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -123,6 +123,21 @@ def normal_f32(n: int, seed: int) -> np.ndarray:
         bits[pos_pay] = np.uint32(0x7F800000) | payload[: len(pos_pay)]
         bits[neg_pay] = np.uint32(0xFF800000) | payload[: len(neg_pay)]
     return bits.view(np.float32)
+
+
+def segment_sizes(num: int, lo: int, hi: int, seed: int) -> np.ndarray:
+    """Sizes of a batch of independent arrays, log-uniform on [lo, hi] (the
+    batched workload: thousands of arrays of uneven size)."""
+    g = _rng(seed)
+    x = np.exp(g.uniform(np.log(lo), np.log(hi + 1), size=num))
+    return np.minimum(np.floor(x).astype(np.int64), hi)
+
+
+def offsets_of(sizes) -> np.ndarray:
+    """Exclusive prefix sums of sizes, with the total appended (int64)."""
+    o = np.zeros(len(sizes) + 1, dtype=np.int64)
+    np.cumsum(np.asarray(sizes, dtype=np.int64), out=o[1:])
+    return o
 
 
 def index_payload(n: int) -> np.ndarray:
