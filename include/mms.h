@@ -78,14 +78,18 @@ mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws,
                             void* stream, const mms_options* opt);
 
 /* Sorts (key, 32-bit value) pairs stably by key (Sec. 4 with the order of
- * Sec. 4.1 read on (key, position)); values move with keys.  4-byte keys
- * (u32, f32), n < 2^32.  The rounds run on unique 64-bit composites
+ * Sec. 4.1 read on (key, position)); values move with keys.  n < 2^32.
+ * 4-byte keys (u32, f32): the rounds run on unique 64-bit composites
  * (ordered key << 32 | position) and a last kernel gathers the values.
+ * 8-byte keys (u64): two stable 4-byte passes, the low key halves first, then
+ * the high halves of the items in that order, whose ties keep the first
+ * pass's order (the textbook LSD composition of stable sorts); a last kernel
+ * applies the resulting permutation to keys and values.
  * Workspace: mms_sort_workspace_bytes(kt, n, 1), or NULL (allocated and freed
- * stream-ordered).  8-byte keys return MMS_ERR_UNSUPPORTED.  opt: as for
- * mms_sort_keys_ex; its events are recorded before the value copy, after the
- * base case, after each splitter and merge pass, and after the value gather;
- * tile_items may be 0, 2048 or 4096 (composite tiles). */
+ * stream-ordered).  opt: as for mms_sort_keys_ex; its events are recorded
+ * before the value copy, after the base case, after each splitter and merge
+ * pass, and after the value gather (for 8-byte keys, those of both passes in
+ * turn); tile_items may be 0, 2048 or 4096 (composite tiles). */
 mms_status mms_sort_pairs(mms_key_type kt, void* d_keys, uint32_t* d_values, size_t n, void* d_ws,
                           size_t ws_bytes, void* stream);
 mms_status mms_sort_pairs_ex(mms_key_type kt, void* d_keys, uint32_t* d_values, size_t n,
@@ -172,8 +176,9 @@ size_t mms_segmented_workspace_bytes(mms_key_type kt, size_t total_n, size_t num
 int mms_segmented_rounds(mms_key_type kt, size_t max_segment_items, int with_values,
                          const mms_segmented_options* opt);
 
-/* Sorts every segment of d_keys in place; with d_values (4-byte keys only,
- * total_n < 2^32) the 32-bit values move with their keys.  d_ws (256-byte
+/* Sorts every segment of d_keys in place; with d_values (total_n < 2^32) the
+ * 32-bit values move with their keys (8-byte keys: two stable passes, as for
+ * mms_sort_pairs).  d_ws (256-byte
  * aligned, mms_segmented_workspace_bytes) is required.  Asynchronous on
  * `stream`. */
 mms_status mms_segmented_sort(mms_key_type kt, void* d_keys, uint32_t* d_values,

@@ -34,6 +34,9 @@ size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct WsLayout {
   size_t keys_off, vals_off, table_off, total;
   size_t comp0_off, comp1_off;   // key-value sort: the two 64-bit composite buffers
+  // key-value sort of 8-byte keys: a 4-byte half of every key, the position
+  // list of the two passes, and copies of the keys and values
+  size_t half_off, perm_off, kcopy_off, vcopy_off;
 };
 
 // Key-only sort: status | ping-pong copy of the keys | pivot table.
@@ -58,6 +61,13 @@ WsLayout ws_layout(mms_key_type kt, size_t n, int with_values) {
   L.keys_off = L.comp0_off;
   const size_t rows = (n + 2047) / 2048 + 1;
   L.total = round_up(L.table_off + rows * mms::kMaxFanout * sizeof(long long), 256);
+  if (kt == MMS_KEY_U64) {
+    L.half_off = L.total;
+    L.perm_off = round_up(L.half_off + n * 4, 256);
+    L.kcopy_off = round_up(L.perm_off + n * 4, 256);
+    L.vcopy_off = round_up(L.kcopy_off + n * 8, 256);
+    L.total = round_up(L.vcopy_off + n * 4, 256);
+  }
   return L;
 }
 
@@ -229,38 +239,16 @@ mms_status mms_sort_keys(mms_key_type kt, void* d_keys, size_t n, void* d_ws, si
   return mms_sort_keys_ex(kt, d_keys, n, d_ws, ws_bytes, stream, nullptr);
 }
 
-mms_status mms_sort_pairs_ex(mms_key_type kt, void* d_keys, uint32_t* d_values, size_t n,
-                             void* d_ws, size_t ws_bytes, void* stream, const mms_options* opt) {
-  if (!valid_kt(kt)) return fail(MMS_ERR_INVALID_ARG, "unknown key type%s");
-  if (kt == MMS_KEY_U64)
-    return fail(MMS_ERR_UNSUPPORTED, "key-value sorting takes 4-byte keys (u32, f32)%s");
-  if (n <= 1) return MMS_OK;
-  if (n > 0xFFFFFFFEull) return fail(MMS_ERR_UNSUPPORTED, "key-value sorting takes fewer than 2^32 items%s");
-  if (!d_keys || !d_values || !aligned16(d_keys) || !aligned16(d_values))
-    return fail(MMS_ERR_INVALID_ARG, "keys/values pointer null or not 16-byte aligned%s");
-  if (opt && opt->fanout != 0 && (opt->fanout < 2 || opt->fanout > mms::kMaxFanout))
-    return fail(MMS_ERR_INVALID_ARG, "fanout must be 0 or in 2..32%s");
-  if (opt && opt->tile_items != 0 && opt->tile_items != 2048 && opt->tile_items != 4096)
-    return fail(MMS_ERR_INVALID_ARG, "tile_items of a key-value sort must be 0, 2048 or 4096%s");
-  const WsLayout L = ws_layout(kt, n, 1);
-  cudaStream_t s = (cudaStream_t)stream;
-  bool owned = false;
-  if (d_ws) {
-    if (!aligned16(d_ws)) return fail(MMS_ERR_INVALID_ARG, "workspace not 16-byte aligned%s");
-    if (ws_bytes < L.total) return fail(MMS_ERR_NO_MEMORY, "workspace smaller than mms_sort_workspace_bytes()%s");
-  } else {
-    cudaError_t e = cudaMallocAsync(&d_ws, L.total, s);
-    if (e != cudaSuccess) return fail(MMS_ERR_NO_MEMORY, "cudaMallocAsync of the workspace failed%s");
-    e = cudaMemsetAsync(d_ws, 0, kStatusBytes, s);
-    if (e != cudaSuccess) { cudaFreeAsync(d_ws, s); return cuda_fail(e, "workspace init"); }
-    owned = true;
-  }
-  unsigned char* ws = static_cast<unsigned char*>(d_ws);
+// The 4-byte key-value sort on the composite buffers of layout L (the values
+// are copied first, so d_keys / d_values are overwritten only by the last
+// kernel): composite base case, merge rounds, key write-back and value gather.
+static mms_status pairs32_run(bool is_f32, void* d_keys, uint32_t* d_values, size_t n,
+                              unsigned char* ws, const WsLayout& L, cudaStream_t s,
+                              const mms_options* opt, int& ev) {
   int* dev_err = reinterpret_cast<int*>(ws);
   void* comp[2] = {ws + L.comp0_off, ws + L.comp1_off};
   void* vcopy = ws + L.vals_off;
   long long* table = reinterpret_cast<long long*>(ws + L.table_off);
-  const bool is_f32 = kt == MMS_KEY_F32;
 
   // The rounds run on 8-byte composites with the 8-byte tile geometry.
   mms_options o8{};
@@ -271,7 +259,6 @@ mms_status mms_sort_pairs_ex(mms_key_type kt, void* d_keys, uint32_t* d_values, 
   int K[64];
   const int rounds = plan_rounds(8, n, &o8, K, 64);
 
-  int ev = 0;
   auto mark = [&]() {
     if (opt && opt->events && ev < opt->num_events && opt->events[ev])
       cudaEventRecord((cudaEvent_t)opt->events[ev], s);
@@ -301,6 +288,59 @@ mms_status mms_sort_pairs_ex(mms_key_type kt, void* d_keys, uint32_t* d_values, 
     st = check_launch(mms::launch_pairs_finalize(is_f32, comp[cur], vcopy, d_keys, d_values,
                                                  (long long)n, s), "pairs_finalize");
   mark();
+  return st;
+}
+
+mms_status mms_sort_pairs_ex(mms_key_type kt, void* d_keys, uint32_t* d_values, size_t n,
+                             void* d_ws, size_t ws_bytes, void* stream, const mms_options* opt) {
+  if (!valid_kt(kt)) return fail(MMS_ERR_INVALID_ARG, "unknown key type%s");
+  if (n <= 1) return MMS_OK;
+  if (n > 0xFFFFFFFEull) return fail(MMS_ERR_UNSUPPORTED, "key-value sorting takes fewer than 2^32 items%s");
+  if (!d_keys || !d_values || !aligned16(d_keys) || !aligned16(d_values))
+    return fail(MMS_ERR_INVALID_ARG, "keys/values pointer null or not 16-byte aligned%s");
+  if (opt && opt->fanout != 0 && (opt->fanout < 2 || opt->fanout > mms::kMaxFanout))
+    return fail(MMS_ERR_INVALID_ARG, "fanout must be 0 or in 2..32%s");
+  if (opt && opt->tile_items != 0 && opt->tile_items != 2048 && opt->tile_items != 4096)
+    return fail(MMS_ERR_INVALID_ARG, "tile_items of a key-value sort must be 0, 2048 or 4096%s");
+  const WsLayout L = ws_layout(kt, n, 1);
+  cudaStream_t s = (cudaStream_t)stream;
+  bool owned = false;
+  if (d_ws) {
+    if (!aligned16(d_ws)) return fail(MMS_ERR_INVALID_ARG, "workspace not 16-byte aligned%s");
+    if (ws_bytes < L.total) return fail(MMS_ERR_NO_MEMORY, "workspace smaller than mms_sort_workspace_bytes()%s");
+  } else {
+    cudaError_t e = cudaMallocAsync(&d_ws, L.total, s);
+    if (e != cudaSuccess) return fail(MMS_ERR_NO_MEMORY, "cudaMallocAsync of the workspace failed%s");
+    e = cudaMemsetAsync(d_ws, 0, kStatusBytes, s);
+    if (e != cudaSuccess) { cudaFreeAsync(d_ws, s); return cuda_fail(e, "workspace init"); }
+    owned = true;
+  }
+  unsigned char* ws = static_cast<unsigned char*>(d_ws);
+  int* dev_err = reinterpret_cast<int*>(ws);
+  int ev = 0;
+  mms_status st = MMS_OK;
+  if (kt != MMS_KEY_U64) {
+    st = pairs32_run(kt == MMS_KEY_F32, d_keys, d_values, n, ws, L, s, opt, ev);
+  } else {
+    // Two stable 4-byte passes, low half first (see pairs.cu).
+    void* half = ws + L.half_off;
+    void* perm = ws + L.perm_off;
+    void* kcopy = ws + L.kcopy_off;
+    void* vcopy = ws + L.vcopy_off;
+    st = check_launch(mms::launch_u64_pairs_split(d_keys, d_values, half, perm, kcopy, vcopy,
+                                                  (long long)n, s), "key-value split (8-byte keys)");
+    if (st == MMS_OK)
+      st = pairs32_run(false, half, static_cast<uint32_t*>(perm), n, ws, L, s, opt, ev);
+    if (st == MMS_OK)
+      st = check_launch(mms::launch_u64_pairs_hi(kcopy, perm, half, (long long)n, s),
+                        "key-value high halves (8-byte keys)");
+    if (st == MMS_OK)
+      st = pairs32_run(false, half, static_cast<uint32_t*>(perm), n, ws, L, s, opt, ev);
+    if (st == MMS_OK)
+      st = check_launch(mms::launch_u64_pairs_final(kcopy, vcopy, perm, d_keys, d_values,
+                                                    (long long)n, s),
+                        "key-value permutation (8-byte keys)");
+  }
   if (owned) {
     int word = 0;
     cudaError_t e = cudaMemcpyAsync(&word, dev_err, sizeof word, cudaMemcpyDeviceToHost, s);

@@ -53,6 +53,16 @@ cudaError_t launch_tile_sort_composite(int tile_warps, bool xin, const void* key
 cudaError_t launch_pairs_finalize(bool xout, const void* comp64, const void* vals_src,
                                   void* keys_out, void* vals_out, long long n, cudaStream_t s);
 
+// Key-value sort of 8-byte keys as two stable 4-byte passes (low half, then
+// high half): pass inputs, the high halves in pass-1 order, and the final
+// permutation of keys and values.
+cudaError_t launch_u64_pairs_split(const void* keys, const void* vals, void* lo, void* perm,
+                                   void* kcopy, void* vcopy, long long n, cudaStream_t s);
+cudaError_t launch_u64_pairs_hi(const void* kcopy, const void* perm, void* hi, long long n,
+                                cudaStream_t s);
+cudaError_t launch_u64_pairs_final(const void* kcopy, const void* vcopy, const void* perm,
+                                   void* keys, void* vals, long long n, cudaStream_t s);
+
 // Splitter: co-ranks of every output tile start (tiles of S items) of every
 // group of K runs.
 cudaError_t launch_splitter(int key_bytes, long long S, const void* in, long long n,

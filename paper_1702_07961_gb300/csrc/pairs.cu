@@ -1,4 +1,5 @@
-// pairs.cu -- last step of the key-value sort.  The sort itself runs on unique
+// pairs.cu -- the key-value sort's own kernels.  Last step of the 4-byte
+// key-value sort:  The sort itself runs on unique
 // 64-bit composites (ordered 32-bit key << 32 | original array position), so
 // equal keys keep their input order (stability) and every sorted composite
 // names the position its value came from.  This kernel writes the keys back
@@ -55,6 +56,86 @@ cudaError_t launch_pairs_finalize(bool xout, const void* comp64, const void* val
     pairs_finalize_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(c, vs, ko, vo, n);
   else
     pairs_finalize_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(c, vs, ko, vo, n);
+  return cudaGetLastError();
+}
+
+// ---- key-value sorting of 8-byte keys -----------------------------------------
+//
+// Two stable passes of the 4-byte key-value sort, least significant half
+// first (the textbook LSD composition of stable sorts): pass 1 sorts the
+// items' positions by the low 32 key bits, pass 2 sorts the resulting
+// position list by the high 32 key bits of the items it names.  Equal high
+// halves keep pass 1's order, which is by (low half, position), so the final
+// list is ordered by (key, position): the stable key order.  These kernels
+// prepare the passes and apply the final permutation.
+
+__global__ void __launch_bounds__(256)
+    u64_split_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                     uint32_t* __restrict__ lo, uint32_t* __restrict__ perm,
+                     uint64_t* __restrict__ kcopy, uint32_t* __restrict__ vcopy, long long n,
+                     long long pos0) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t k = keys[i];
+    lo[i] = (uint32_t)k;
+    perm[i] = (uint32_t)(pos0 + i);
+    kcopy[i] = k;
+    vcopy[i] = vals[i];
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    u64_hi_kernel(const uint64_t* __restrict__ kcopy, const uint32_t* __restrict__ perm,
+                  uint32_t* __restrict__ hi, long long n, long long pos0) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    hi[i] = (uint32_t)(kcopy[(long long)perm[i] - pos0] >> 32);
+}
+
+__global__ void __launch_bounds__(256)
+    u64_final_kernel(const uint64_t* __restrict__ kcopy, const uint32_t* __restrict__ vcopy,
+                     const uint32_t* __restrict__ perm, uint64_t* __restrict__ keys,
+                     uint32_t* __restrict__ vals, long long n, long long pos0) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const long long p = (long long)perm[i] - pos0;
+    keys[i] = kcopy[p];
+    vals[i] = vcopy[p];
+  }
+}
+
+static unsigned grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_u64_pairs_split(const void* keys, const void* vals, void* lo, void* perm,
+                                   void* kcopy, void* vcopy, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  u64_split_kernel<<<grid_for(n), 256, 0, s>>>(
+      static_cast<const uint64_t*>(keys), static_cast<const uint32_t*>(vals),
+      static_cast<uint32_t*>(lo), static_cast<uint32_t*>(perm), static_cast<uint64_t*>(kcopy),
+      static_cast<uint32_t*>(vcopy), n, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_u64_pairs_hi(const void* kcopy, const void* perm, void* hi, long long n,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  u64_hi_kernel<<<grid_for(n), 256, 0, s>>>(static_cast<const uint64_t*>(kcopy),
+                                             static_cast<const uint32_t*>(perm),
+                                             static_cast<uint32_t*>(hi), n, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_u64_pairs_final(const void* kcopy, const void* vcopy, const void* perm,
+                                   void* keys, void* vals, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  u64_final_kernel<<<grid_for(n), 256, 0, s>>>(
+      static_cast<const uint64_t*>(kcopy), static_cast<const uint32_t*>(vcopy),
+      static_cast<const uint32_t*>(perm), static_cast<uint64_t*>(keys),
+      static_cast<uint32_t*>(vals), n, 0);
   return cudaGetLastError();
 }
 

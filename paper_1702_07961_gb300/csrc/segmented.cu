@@ -354,6 +354,30 @@ SegLayout seg_layout(int unit_bytes, bool pairs, size_t total_n, size_t nseg, co
   return L;
 }
 
+// Key-value batches of 8-byte keys: two stable 4-byte passes (low half, then
+// high half; see pairs.cu) over the 4-byte batch layout, plus a 4-byte half
+// of every key, the position list, and copies of the keys and values.
+struct SegLayout64 {
+  SegLayout inner;
+  size_t half, perm, kcopy, vcopy, total;
+};
+
+SegLayout64 seg_layout64(size_t total_n, size_t nseg, const SegPlan& P) {
+  SegLayout64 L{};
+  L.inner = seg_layout(8, true, total_n, nseg, P);
+  size_t o = L.inner.total;
+  L.half = o;
+  o = round_up(o + total_n * 4, 256);
+  L.perm = o;
+  o = round_up(o + total_n * 4, 256);
+  L.kcopy = o;
+  o = round_up(o + total_n * 8, 256);
+  L.vcopy = o;
+  o = round_up(o + total_n * 4, 256);
+  L.total = o;
+  return L;
+}
+
 int sm_count() {
   static int sms = 0;
   if (!sms) {
@@ -532,7 +556,6 @@ mms_status seg_prepare(mms_key_type kt, bool pairs, int tw, int kmax) {
 bool seg_args_ok(mms_key_type kt, const uint32_t* vals, const mms_segmented_options* opt,
                  const char** why) {
   if (kt != MMS_KEY_U32 && kt != MMS_KEY_U64 && kt != MMS_KEY_F32) { *why = "unknown key type"; return false; }
-  if (vals && kt == MMS_KEY_U64) { *why = "key-value batches take 4-byte keys (u32, f32)"; return false; }
   if (opt && opt->tile_items) {
     const int unit = (vals || kt == MMS_KEY_U64) ? 8 : 4;
     const int w = opt->tile_items / 1024;
@@ -569,13 +592,15 @@ size_t mms_segmented_workspace_bytes(mms_key_type kt, size_t total_n, size_t num
   const size_t mx = (opt && opt->max_segment_items) ? opt->max_segment_items : total_n;
   P.rounds = max_rounds(P, mx);
   P.nphase = 1 + P.rounds;
+  if (with_values && kt == MMS_KEY_U64) return seg_layout64(total_n, num_segments, P).total;
   return seg_layout(unit, with_values != 0, total_n, num_segments, P).total;
 }
 
 static mms_status seg_sort_impl(mms_key_type kt, void* d_keys, uint32_t* d_values,
                                 const uint64_t* d_offsets, size_t num_segments, size_t total_n,
                                 void* d_ws, size_t ws_bytes, void* stream,
-                                const mms_segmented_options* opt, bool prepare_only) {
+                                const mms_segmented_options* opt, bool prepare_only,
+                                bool clear_status = true) {
   const char* why = "";
   if (!seg_args_ok(kt, d_values, opt, &why)) return seg_fail(MMS_ERR_INVALID_ARG, why);
   if (num_segments == 0 || total_n == 0) return MMS_OK;
@@ -593,6 +618,36 @@ static mms_status seg_sort_impl(mms_key_type kt, void* d_keys, uint32_t* d_value
   P.rounds = max_rounds(P, mx);
   if (P.rounds > kMaxRounds) return seg_fail(MMS_ERR_UNSUPPORTED, "too many merge rounds");
   P.nphase = 1 + P.rounds;
+  if (pairs && kt == MMS_KEY_U64) {
+    // Two stable passes of the 4-byte key-value batch, low key halves first.
+    const SegLayout64 L = seg_layout64(total_n, num_segments, P);
+    if (!d_ws || ((uintptr_t)d_ws & 255u)) return seg_fail(MMS_ERR_INVALID_ARG, "workspace missing or not 256-byte aligned");
+    if (ws_bytes < L.total) return seg_fail(MMS_ERR_NO_MEMORY, "workspace smaller than mms_segmented_workspace_bytes()");
+    unsigned char* ws = static_cast<unsigned char*>(d_ws);
+    void* half = ws + L.half;
+    uint32_t* perm = reinterpret_cast<uint32_t*>(ws + L.perm);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prepare_only)
+      return seg_sort_impl(MMS_KEY_U32, half, perm, d_offsets, num_segments, total_n, d_ws,
+                           L.inner.total, stream, opt, true);
+    if (clear_status && cudaMemsetAsync(d_ws, 0, sizeof(int), s) != cudaSuccess)
+      return seg_fail(MMS_ERR_CUDA, "status word");
+    if (launch_u64_pairs_split(d_keys, d_values, half, perm, ws + L.kcopy, ws + L.vcopy,
+                               (long long)total_n, s) != cudaSuccess)
+      return seg_fail(MMS_ERR_CUDA, "key-value split (8-byte keys)");
+    mms_status st = seg_sort_impl(MMS_KEY_U32, half, perm, d_offsets, num_segments, total_n, d_ws,
+                                  L.inner.total, stream, opt, false, false);
+    if (st != MMS_OK) return st;
+    if (launch_u64_pairs_hi(ws + L.kcopy, perm, half, (long long)total_n, s) != cudaSuccess)
+      return seg_fail(MMS_ERR_CUDA, "key-value high halves (8-byte keys)");
+    st = seg_sort_impl(MMS_KEY_U32, half, perm, d_offsets, num_segments, total_n, d_ws,
+                       L.inner.total, stream, opt, false, false);
+    if (st != MMS_OK) return st;
+    if (launch_u64_pairs_final(ws + L.kcopy, ws + L.vcopy, perm, d_keys, d_values,
+                               (long long)total_n, s) != cudaSuccess)
+      return seg_fail(MMS_ERR_CUDA, "key-value permutation (8-byte keys)");
+    return MMS_OK;
+  }
   const SegLayout L = seg_layout(unit, pairs, total_n, num_segments, P);
   if (L.per_phase > 0x7FFFFFFFll) return seg_fail(MMS_ERR_UNSUPPORTED, "too many tiles per phase");
   if (!d_ws || ((uintptr_t)d_ws & 255u)) return seg_fail(MMS_ERR_INVALID_ARG, "workspace missing or not 256-byte aligned");
@@ -629,7 +684,8 @@ static mms_status seg_sort_impl(mms_key_type kt, void* d_keys, uint32_t* d_value
     return MMS_ERR_CUDA;
   };
   mark();
-  mms_status st = chk(cudaMemsetAsync(dev_err, 0, sizeof(int), s), "status word");
+  mms_status st = clear_status ? chk(cudaMemsetAsync(dev_err, 0, sizeof(int), s), "status word")
+                               : MMS_OK;
   if (st == MMS_OK) {
     seg_plan_kernel<<<(unsigned)((nseg + 255) / 256), 256, 0, s>>>(off, nseg, total_n, P, segK, segR,
                                                                   counts, dev_err);

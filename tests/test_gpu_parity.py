@@ -278,11 +278,23 @@ def test_pairs_f32_specials(gpu):
     assert_bits_equal(gv, wv)
 
 
-def test_pairs_u64_is_unsupported(gpu):
-    tk = to_dev(synth.uniform(100, 1, np.uint64))
-    tv = to_dev(synth.index_payload(100))
-    with pytest.raises(gpu.MMSError):
-        gpu.sort_pairs(tk, tv, kt=gpu.KEY_U64)
+@pytest.mark.parametrize("n,kind", [(2, "uniform"), (777, "uniform"), (4096 * 31 + 9, "hi_dups"),
+                                    (4096 * 31 + 9, "lo_dups"), (1 << 20, "both_dups")])
+def test_pairs_u64_two_passes(gpu, n, kind):
+    """8-byte keys with values: two stable 4-byte passes (low half, then high
+    half); duplicates confined to one half or both exercise the tie rules."""
+    keys = synth.uniform(n, 41 + n, np.uint64)
+    if kind == "hi_dups":       # high halves from 5 values: ties decided by the low halves
+        keys = (keys & np.uint64(0xFFFFFFFF)) | ((keys >> np.uint64(32)) % np.uint64(5) << np.uint64(32))
+    elif kind == "lo_dups":     # low halves from 3 values
+        keys = (keys & np.uint64(0xFFFFFFFF00000000)) | (keys % np.uint64(3))
+    elif kind == "both_dups":   # whole keys repeat: stability decides the values' order
+        keys = ((keys % np.uint64(7)) << np.uint64(32)) | (keys % np.uint64(3))
+    vals = synth.uniform(n, 42 + n, np.uint32)
+    wk, wv = oracle.sort(keys, vals)
+    gk, gv = gpu_sort_pairs(gpu, keys, vals)
+    assert_bits_equal(gk, wk)
+    assert_bits_equal(gv, wv)
 
 
 @pytest.mark.slow

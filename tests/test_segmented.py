@@ -77,10 +77,12 @@ def test_segmented_keys_match_oracle(gpu, dtype):
     assert np.array_equal(bits(got), bits(want))
 
 
-@pytest.mark.parametrize("dtype", [np.uint32, np.float32])
+@pytest.mark.parametrize("dtype", [np.uint32, np.float32, np.uint64])
 def test_segmented_pairs_match_oracle(gpu, dtype):
     keys, off = batch(23, dtype)
     keys[::3] = keys[1::3][: keys[::3].size] if keys.size > 2 else keys[::3]     # many equal keys
+    if np.dtype(dtype) == np.uint64:        # and equal high halves with distinct low halves
+        keys[1::4] = (keys[1::4] & np.uint64(0xFFFFFFFF)) | np.uint64(0x1234 << 32)
     vals = synth.index_payload(keys.size)
     got_k, got_v = run(gpu, keys, off, vals)
     want_k, want_v = oracle.segmented_sort(keys, off, vals)
