@@ -48,11 +48,12 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=1 << 25)
-    p.add_argument("--workload", default="sort", choices=["sort", "batched"],
+    p.add_argument("--workload", default="sort", choices=["sort", "batched", "serve"],
                    help="sort: one 10^8-key array per step; batched: 20000 arrays of "
                         "log-uniform size in [2^8, 2^20] with uint32 payloads per step")
     p.add_argument("--arrays", type=int, default=20000)
     p.add_argument("--retune", action="store_true", help="batched: re-run the autotuner")
+    p.add_argument("--requests", type=int, default=100, help="serve: requests per arrival-rate run")
     return p.parse_args()
 
 
@@ -374,12 +375,123 @@ def run_batched(args):
     return 0
 
 
+def run_serve(args):
+    """C5: Poisson arrivals of sort requests, sizes log-uniform in [2^10, 2^26],
+    key type uniform over {u32, u64, f32}, half with uint32 values, 40 GB budget;
+    the continuous-batching server against serial plain sorts at swept rates."""
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_1702_07961_gb300 as mms
+    from paper_1702_07961_gb300 import serve
+    import synth
+
+    count = args.requests
+    sizes = synth.segment_sizes(count, 1 << 10, 1 << 26, 11 + rank)
+    rng = np.random.default_rng(12 + rank)
+    kts = rng.choice([mms.KEY_U32, mms.KEY_U64, mms.KEY_F32], size=count)
+    with_vals = rng.random(count) < 0.5
+    reqs = []
+    for i in range(count):
+        n, kt = int(sizes[i]), int(kts[i])
+        seed = 1000 * (rank + 1) + i
+        keys = (synth.normal_f32(n, seed) if kt == mms.KEY_F32 else
+                synth.uniform(n, seed, np.uint64 if kt == mms.KEY_U64 else np.uint32))
+        vals = synth.index_payload(n) if with_vals[i] else None
+        reqs.append(serve.Request(i, kt, keys, vals, 0.0))
+    for r in reqs:
+        serve.SortServer.prepare(r)
+    total_keys = int(sizes.sum())
+
+    def reset(arrivals):
+        for r, a in zip(reqs, arrivals):
+            r.arrival, r.start, r.finish = float(a), None, None
+
+    # Serial capacity: every request waiting at t = 0, served one at a time.
+    reset(np.zeros(count))
+    serve.serve_serial(reqs)                          # warm-up
+    reset(np.zeros(count))
+    serve.serve_serial(reqs)
+    busy = max(r.finish for r in reqs)
+    capacity = count / busy
+    def bits(t):                                      # compare bit patterns (NaN keys included)
+        a = t.numpy()
+        return a.view(np.uint64 if a.dtype.itemsize == 8 else np.uint32)
+
+    alone = [(bits(r.out_keys).copy(), None if r.out_values is None else bits(r.out_values).copy())
+             for r in reqs]
+
+    srv = serve.SortServer(budget_bytes=40 << 30, slots=4)
+    reset(np.zeros(count))
+    srv.run(reqs)                                     # warm-up of the server's kernels and arena
+    torch.cuda.synchronize()
+    sweep = []
+    sampler = ClockSampler(gpu_uuid(local))
+    sampler.start()
+    t0 = time.time()
+    for f in (0.5, 1.0, 2.0, 4.0):
+        rate = f * capacity
+        arr = serve.poisson_arrivals(count, rate, 77)
+        reset(arr)
+        g0, c0 = srv.groups, srv.coalesced
+        srv.max_inflight = 0
+        srv.run(reqs)
+        s_srv = serve.summarize(reqs)
+        same = all(np.array_equal(bits(r.out_keys), a[0]) and
+                   (a[1] is None or np.array_equal(bits(r.out_values), a[1])) for r, a in zip(reqs, alone))
+        reset(arr)
+        serve.serve_serial(reqs)
+        s_ser = serve.summarize(reqs)
+        sweep.append({"rate_per_s": rate, "load_vs_serial_capacity": f, "server": s_srv, "serial": s_ser,
+                      "groups": srv.groups - g0, "coalesced_requests": srv.coalesced - c0,
+                      "max_groups_in_flight": srv.max_inflight, "same_as_alone": same})
+    t1 = time.time()
+    sampler.stop()
+    ok = all(x["same_as_alone"] for x in sweep)
+    # a sample of small requests against the CPU oracle
+    for r, a in zip(reqs, alone):
+        if r.n <= 1 << 16:
+            wk, wv = oracle.sort(r.keys, r.values)
+            ok &= bool(np.array_equal(a[0], wk.view(a[0].dtype)))
+            if wv is not None:
+                ok &= bool(np.array_equal(a[1].view(np.uint32), wv))
+    if not ok:
+        raise SystemExit("bench: served results differ from the same requests served alone")
+    top = sweep[-1]
+    out = {
+        "metric": "served Gkeys/s and p99 latency (Poisson arrivals)", "value": top["server"]["gkeys_per_s"],
+        "unit": "Gkeys/s", "n_gpus": 1, "steps": len(sweep), "warmup": 1,
+        "ms_per_step": top["server"]["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "mixed(u32,u64,f32)", "data": "synthetic",
+        "config": {"workload": f"{count} requests, sizes log-uniform in [2^10, 2^26] ({total_keys} keys), key type "
+                               "uniform over {u32, u64, f32}, half with uint32 values, keys from host memory and "
+                               "results back to host; Poisson arrivals at 0.5, 1, 2 and 4 times the serial "
+                               "capacity; 40 GB device budget, 4 launch slots, requests <= 2^20 keys coalesced",
+                   "global_batch": total_keys, "seq_len": None, "parallelism": "single GPU",
+                   "serial_capacity_req_per_s": capacity},
+        "sweep": sweep,
+        "latency_ms_p50": top["server"]["latency_ms_p50"], "latency_ms_p99": top["server"]["latency_ms_p99"],
+        "serial_latency_ms_p99": top["serial"]["latency_ms_p99"],
+        "verified": ok,
+        "clocks": sampler.summary(t0, t1),
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serve":
+        return run_serve(args)
     import numpy as np
     import torch
 
