@@ -264,6 +264,32 @@ def _pins_hold() -> bool:
         return False
 
 
+def test_segmented_sort_closed_form_and_brute_force():
+    """Batched sort: each segment of concatenated permutations sorts to its own
+    iota (closed form) and the index payload becomes each segment's inverse
+    permutation; tiny segments of words with repeats match brute force."""
+    sizes = [0, 1, 5, 300, 0, 2, 4097]
+    parts = [synth.permutation(n, 40 + i) for i, n in enumerate(sizes)]
+    keys = np.concatenate(parts).astype(np.uint32)
+    off = synth.offsets_of(sizes)
+    vals = synth.index_payload(keys.size)
+    k, v = oracle.segmented_sort(keys, off, vals)
+    for i, n in enumerate(sizes):
+        a, b = int(off[i]), int(off[i + 1])
+        assert np.array_equal(k[a:b], np.arange(n, dtype=np.uint32))
+        inv = np.empty(n, dtype=np.uint32)
+        inv[parts[i]] = np.arange(n, dtype=np.uint32)
+        assert np.array_equal(v[a:b] - np.uint32(a), inv)
+    words = np.array([2, 0, 1, 0, 2, 1, 1, 0, 2], dtype=np.uint32)
+    off = np.array([0, 4, 4, 9], dtype=np.int64)
+    k, v = oracle.segmented_sort(words, off, np.arange(9, dtype=np.uint32))
+    for a, b in [(0, 4), (4, 9)]:
+        p = brute_force_stable_perm(list(words[a:b]))
+        assert list(v[a:b]) == [a + i for i in p]
+    # no item crosses a segment boundary
+    assert sorted(k[:4].tolist()) == sorted(words[:4].tolist())
+
+
 @pytest.mark.parametrize("mutation", [1, 2, 3, 4, 5])
 def test_planted_mistakes_are_caught(mutation):
     assert _pins_hold()
