@@ -27,6 +27,12 @@
 
 namespace mms {
 
+// Control area after a merge CTA's mbarrier: the merge-tree node table (8
+// fields x 32 nodes) and four scalars, written by warp 0 for the whole CTA.
+constexpr int kCtlNodeFields = 8;
+constexpr int kCtlScalars = 8;
+constexpr size_t kMergeCtlBytes = sizeof(int) * (kCtlNodeFields * 32 + kCtlScalars);
+
 // Shared-memory geometry of a merge CTA for fanout K.  X: the staged
 // segments, each at a 16-byte aligned span start R_r (up to 2E-2 items of
 // alignment slack and 32 items of transpose slack per segment), and the odd
@@ -37,9 +43,9 @@ struct MergeGeom {
   static constexpr int S = WARPS * kBlockItems;
   static constexpr int kSlack = 32;
   __host__ __device__ static constexpr int cap(int K) { return S + K * (2 * E + kSlack) + E; }
-  // control block: mbarrier (8), error flag (4), pad (4)
+  // control block: mbarrier (16 bytes with padding), then the node table
   __host__ __device__ static constexpr size_t bytes(int K) {
-    return sizeof(KeyT) * 2 * (size_t)cap(K) + 16;
+    return sizeof(KeyT) * 2 * (size_t)cap(K) + 16 + kMergeCtlBytes;
   }
 };
 
@@ -82,130 +88,151 @@ __device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   const long long gstart = g * run_len * K;
-  const long long grest = n - gstart;
-  const long long gsize = grest < run_len * K ? grest : run_len * K;
-  const long long tiles_here = (gsize + S - 1) / S;
-
-  // Segment of run `lane` for this tile (every warp computes the same).
-  const bool act = lane < K;
-  const long long rstart = gstart + (long long)lane * run_len;
-  long long rlen = n - rstart;
-  rlen = rlen < 0 ? 0 : (rlen > run_len ? run_len : rlen);
-  long long lo = 0, hi = 0;
-  if (act) {
-    lo = (j == 0) ? 0 : lo_row[lane];
-    hi = (j + 1 < tiles_here) ? hi_row[lane] : rlen;
-  }
-  // The pivot rows must describe segments inside their runs whose lengths sum
-  // to this tile's size; anything else would overrun the staging buffer.
-  const long long want = (gsize - j * S) < S ? (gsize - j * S) : S;
-  {
-    const bool bad_seg = act && (lo < 0 || hi < lo || hi > rlen);
-    long long sum = act ? hi - lo : 0;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (__any_sync(0xffffffffu, bad_seg) || sum != want || K > kMaxFanout || K < 2 ||
-        (smem_u32addr(smem_raw) & 1023u) != 0) {
-      if (threadIdx.x == 0) set_device_error(dev_err, kDevErrInternal);
-      return false;                                    // uniform over the CTA
-    }
-  }
-  const long long gsrc = rstart + lo;                  // first item, index into `in`
-  const int len = act ? (int)(hi - lo) : 0;
-  // `in` itself may sit off the 16-byte grid (a segment of a batch): the bulk
-  // copies align on absolute addresses.
-  const int in_mis = (int)(((uintptr_t)in / sizeof(KeyT)) & (E - 1));
-  const int head = act ? (int)((in_mis + gsrc) % E) : 0;   // items copied before the segment
-  const int span = (head + len + E - 1) / E * E + G::kSlack;   // staged span + transpose slack
-  int incl = span;
-  int lincl = len;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int x = __shfl_up_sync(0xffffffffu, incl, o);
-    const int y = __shfl_up_sync(0xffffffffu, lincl, o);
-    if (lane >= o) {
-      incl += x;
-      lincl += y;
-    }
-  }
-  const int R = incl - span;                           // span start of segment `lane`
-  const int lpre = lincl - len;                        // items in segments before `lane`
-  // Bulk part: from gsrc - head to the last 16-byte boundary (of absolute
-  // addresses) inside the segment; the rest by plain loads.
-  const long long bulk_lo = gsrc - head;
-  const long long bulk_hi = (in_mis + gsrc + len) / E * E - in_mis;
-  const unsigned bulk_bytes =
-      (act && bulk_hi > bulk_lo) ? (unsigned)((bulk_hi - bulk_lo) * sizeof(KeyT)) : 0u;
+  int* ctl = reinterpret_cast<int*>(bar + 2);          // node table and scalars (see above)
 
   // Every thread is past the previous tile (whose store has read its shared
   // memory) before the staging copies overwrite the buffer.
   __syncthreads();
   if (warp == 0) {
-    unsigned total = bulk_bytes;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
-    if (lane == 0) mbar_arrive_expect_tx(bar, total);
-    __syncwarp();
-    if (bulk_bytes) bulk_g2s(bufX + R, in + bulk_lo, bulk_bytes, bar);
-  } else if (warp == 1) {
-    // Ragged ends, one segment at a time, consecutive lanes -> consecutive words.
-    for (int r = 0; r < K; ++r) {
-      const long long s_src = __shfl_sync(0xffffffffu, gsrc, r);
-      const int s_len = __shfl_sync(0xffffffffu, len, r);
-      const int s_off = __shfl_sync(0xffffffffu, R + head, r);
-      const long long s_bhi = __shfl_sync(0xffffffffu, bulk_hi, r);
-      const long long s_blo = __shfl_sync(0xffffffffu, bulk_lo, r);
-      const long long from = (s_bhi > s_blo) ? s_bhi : s_src;   // first item not bulk-copied
-      const long long e = from + lane;
-      if (e < s_src + s_len) bufX[s_off + (int)(e - s_src)] = in[e];
+    // Warp 0 alone plans the tile: one lane per run, one lane per tree node.
+    const long long grest = n - gstart;
+    const long long gsize = grest < run_len * K ? grest : run_len * K;
+    const long long tiles_here = (gsize + S - 1) / S;
+    const bool act = lane < K;
+    const long long rstart = gstart + (long long)lane * run_len;
+    long long rlen = n - rstart;
+    rlen = rlen < 0 ? 0 : (rlen > run_len ? run_len : rlen);
+    long long lo = 0, hi = 0;
+    if (act) {
+      lo = (j == 0) ? 0 : lo_row[lane];
+      hi = (j + 1 < tiles_here) ? hi_row[lane] : rlen;
     }
-  }
-
-  // Merge-tree nodes, one per lane, in level order: node (level l >= 1, pair q)
-  // merges child A = segments [q*2^l, q*2^l + 2^(l-1)) and child B = the rest
-  // of [q*2^l, (q+1)*2^l) (clipped to K).  Every warp derives the same table.
-  int nl = 0, nnodes = 0, c_level = 0, c_pair = 0;
-  {
-    int cnt = K, idx = 0;
-    for (int l = 1; cnt > 1; ++l) {
-      const int pairs = (cnt + 1) >> 1;
-      if (lane >= idx && lane < idx + pairs) {
-        c_level = l;
-        c_pair = lane - idx;
+    // The pivot rows must describe segments inside their runs whose lengths
+    // sum to this tile's size; anything else would overrun the staging buffer.
+    const long long want = (gsize - j * S) < S ? (gsize - j * S) : S;
+    const bool bad_seg = act && (lo < 0 || hi < lo || hi > rlen);
+    long long sum = act ? hi - lo : 0;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    const bool bad = __any_sync(0xffffffffu, bad_seg) || sum != want || K > kMaxFanout || K < 2 ||
+                     (smem_u32addr(smem_raw) & 1023u) != 0;
+    if (lane == 0) {
+      ctl[kCtlNodeFields * 32 + 2] = (int)want;
+      ctl[kCtlNodeFields * 32 + 3] = bad ? 1 : 0;
+    }
+    if (!bad) {
+      const long long gsrc = rstart + lo;              // first item, index into `in`
+      const int len = act ? (int)(hi - lo) : 0;
+      // `in` itself may sit off the 16-byte grid (a segment of a batch): the
+      // bulk copies align on absolute addresses.
+      const int in_mis = (int)(((uintptr_t)in / sizeof(KeyT)) & (E - 1));
+      const int head = act ? (int)((in_mis + gsrc) % E) : 0;   // items copied before the segment
+      const int span = (head + len + E - 1) / E * E + G::kSlack;   // staged span + transpose slack
+      int incl = span;
+      int lincl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, incl, o);
+        const int y = __shfl_up_sync(0xffffffffu, lincl, o);
+        if (lane >= o) {
+          incl += x;
+          lincl += y;
+        }
       }
-      idx += pairs;
-      cnt = pairs;
-      nl = l;
-    }
-    nnodes = idx;
-  }
-  const bool is_node = lane < nnodes;
-  const int first = c_pair << c_level;                  // first segment of the node
-  const int mid = first + (1 << (c_level > 0 ? c_level - 1 : 0));
-  const int last = first + (1 << c_level);
-  auto seg_pre = [&](int s) {                           // items in segments [0, s)
-    const int ss = s < K ? s : K;
-    const int v = __shfl_sync(0xffffffffu, lpre, ss & 31);
-    return ss >= K ? (int)want : v;
-  };
-  const int pf = seg_pre(first), pm = seg_pre(mid), pl = seg_pre(last);
-  const int rf = __shfl_sync(0xffffffffu, R, first & 31);
-  const int hf = __shfl_sync(0xffffffffu, head, first & 31);
-  const int rm = __shfl_sync(0xffffffffu, R, mid & 31);
-  const int hm = __shfl_sync(0xffffffffu, head, mid & 31);
-  const int c_lenA = is_node ? pm - pf : 0;
-  const int c_lenB = is_node ? pl - pm : 0;
-  const int c_offA = (c_level == 1) ? rf + hf : rf;     // staged segment vs. child output
-  const int c_offB = (mid < K) ? ((c_level == 1) ? rm + hm : rm) : 0;
-  const int c_out = rf;
-  const int c_nb = (c_lenA + c_lenB + kBlockItems - 1) / kBlockItems;
-  int c_first = c_nb;
+      const int R = incl - span;                       // span start of segment `lane`
+      const int lpre = lincl - len;                    // items in segments before `lane`
+      // Bulk part: from gsrc - head to the last 16-byte boundary (of absolute
+      // addresses) inside the segment; the rest by plain loads.
+      const long long bulk_lo = gsrc - head;
+      const long long bulk_hi = (in_mis + gsrc + len) / E * E - in_mis;
+      const unsigned bulk_bytes =
+          (act && bulk_hi > bulk_lo) ? (unsigned)((bulk_hi - bulk_lo) * sizeof(KeyT)) : 0u;
+      unsigned total = bulk_bytes;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int x = __shfl_up_sync(0xffffffffu, c_first, o);
-    if (lane >= o) c_first += x;
+      for (int o = 16; o >= 1; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+      if (lane == 0) mbar_arrive_expect_tx(bar, total);
+      __syncwarp();
+      if (bulk_bytes) bulk_g2s(bufX + R, in + bulk_lo, bulk_bytes, bar);
+      // Ragged ends, one segment at a time, consecutive lanes -> consecutive words.
+      for (int r = 0; r < K; ++r) {
+        const long long s_src = __shfl_sync(0xffffffffu, gsrc, r);
+        const int s_len = __shfl_sync(0xffffffffu, len, r);
+        const int s_off = __shfl_sync(0xffffffffu, R + head, r);
+        const long long s_bhi = __shfl_sync(0xffffffffu, bulk_hi, r);
+        const long long s_blo = __shfl_sync(0xffffffffu, bulk_lo, r);
+        const long long from = (s_bhi > s_blo) ? s_bhi : s_src;   // first item not bulk-copied
+        const long long e = from + lane;
+        if (e < s_src + s_len) bufX[s_off + (int)(e - s_src)] = in[e];
+      }
+
+      // Merge-tree nodes, one per lane, in level order: node (level l >= 1,
+      // pair q) merges child A = segments [q*2^l, q*2^l + 2^(l-1)) and child
+      // B = the rest of [q*2^l, (q+1)*2^l) (clipped to K).
+      int nl = 0, nnodes = 0, c_level = 0, c_pair = 0;
+      {
+        int cnt = K, idx = 0;
+        for (int l = 1; cnt > 1; ++l) {
+          const int pairs = (cnt + 1) >> 1;
+          if (lane >= idx && lane < idx + pairs) {
+            c_level = l;
+            c_pair = lane - idx;
+          }
+          idx += pairs;
+          cnt = pairs;
+          nl = l;
+        }
+        nnodes = idx;
+      }
+      const bool is_node = lane < nnodes;
+      const int first = c_pair << c_level;             // first segment of the node
+      const int mid = first + (1 << (c_level > 0 ? c_level - 1 : 0));
+      const int last = first + (1 << c_level);
+      auto seg_pre = [&](int sg) {                     // items in segments [0, sg)
+        const int ss = sg < K ? sg : K;
+        const int v = __shfl_sync(0xffffffffu, lpre, ss & 31);
+        return ss >= K ? (int)want : v;
+      };
+      const int pf = seg_pre(first), pm = seg_pre(mid), pl = seg_pre(last);
+      const int rf = __shfl_sync(0xffffffffu, R, first & 31);
+      const int hf = __shfl_sync(0xffffffffu, head, first & 31);
+      const int rm = __shfl_sync(0xffffffffu, R, mid & 31);
+      const int hm = __shfl_sync(0xffffffffu, head, mid & 31);
+      const int lenA = is_node ? pm - pf : 0;
+      const int lenB = is_node ? pl - pm : 0;
+      const int nb = (lenA + lenB + kBlockItems - 1) / kBlockItems;
+      int fst = nb;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, fst, o);
+        if (lane >= o) fst += x;
+      }
+      ctl[0 * 32 + lane] = lenA;
+      ctl[1 * 32 + lane] = lenB;
+      ctl[2 * 32 + lane] = (c_level == 1) ? rf + hf : rf;                     // staged segment
+      ctl[3 * 32 + lane] = (mid < K) ? ((c_level == 1) ? rm + hm : rm) : 0;   // vs. child output
+      ctl[4 * 32 + lane] = rf;                                                // output span
+      ctl[5 * 32 + lane] = fst - nb;                                          // first block
+      ctl[6 * 32 + lane] = nb;
+      ctl[7 * 32 + lane] = is_node ? c_level : 0;
+      if (lane == 0) {
+        ctl[kCtlNodeFields * 32 + 0] = nl;
+        ctl[kCtlNodeFields * 32 + 1] = nnodes;
+      }
+    }
   }
-  c_first -= c_nb;
+  __syncthreads();
+  if (ctl[kCtlNodeFields * 32 + 3]) {
+    if (threadIdx.x == 0) set_device_error(dev_err, kDevErrInternal);
+    return false;                                      // uniform over the CTA
+  }
+  const int nl = ctl[kCtlNodeFields * 32 + 0];
+  const int nnodes = ctl[kCtlNodeFields * 32 + 1];
+  const long long want = ctl[kCtlNodeFields * 32 + 2];
+  const bool is_node = lane < nnodes;
+  const int c_lenA = ctl[0 * 32 + lane], c_lenB = ctl[1 * 32 + lane];
+  const int c_offA = ctl[2 * 32 + lane], c_offB = ctl[3 * 32 + lane];
+  const int c_out = ctl[4 * 32 + lane], c_first = ctl[5 * 32 + lane];
+  const int c_nb = ctl[6 * 32 + lane], c_level = ctl[7 * 32 + lane];
 
   // One thread polls the staging barrier; the others wait at the CTA barrier
   // (no issue slots spent polling), which also orders the staged data and the

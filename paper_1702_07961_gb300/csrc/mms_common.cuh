@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "mms_kernels.cuh"
 
 namespace mms {
@@ -118,6 +120,33 @@ __device__ __forceinline__ void lds_if_lt(uint64_t& v, const uint64_t* p, int id
       : "r"(smem_u32addr(p)), "r"(idx), "r"(lim)
       : "memory");
 }
+// Full-block load of register k: v = A-side word when 32k < lim, else the
+// B-side word; one compare with an immediate and two predicated loads at
+// immediate offsets from two base addresses (shared-memory byte addresses).
+template <int K32, int OFF>
+__device__ __forceinline__ void lds_select_imm(uint32_t& v, uint32_t pa, uint32_t pb, int lim) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.gt.s32 q, %3, %4;\n\t@q ld.shared.b32 %0, [%1+%5];\n\t"
+      "@!q ld.shared.b32 %0, [%2+%6];\n\t}\n"
+      : "=r"(v)
+      : "r"(pa), "r"(pb), "r"(lim), "n"(K32), "n"(OFF), "n"(-OFF)
+      : "memory");
+}
+template <int K32, int OFF>
+__device__ __forceinline__ void lds_select_imm(uint64_t& v, uint32_t pa, uint32_t pb, int lim) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.gt.s32 q, %3, %4;\n\t@q ld.shared.b64 %0, [%1+%5];\n\t"
+      "@!q ld.shared.b64 %0, [%2+%6];\n\t}\n"
+      : "=l"(v)
+      : "r"(pa), "r"(pb), "r"(lim), "n"(K32), "n"(OFF), "n"(-OFF)
+      : "memory");
+}
+template <typename KeyT, int... Ks>
+__device__ __forceinline__ void lds_full_block(KeyT (&v)[32], uint32_t pa, uint32_t pb, int lim,
+                                               std::integer_sequence<int, Ks...>) {
+  (lds_select_imm<32 * Ks, 32 * Ks * (int)sizeof(KeyT)>(v[Ks], pa, pb, lim), ...);
+}
+
 // Loads p[0] into v when idx >= lim (signed).
 __device__ __forceinline__ void lds_if_ge(uint32_t& v, const uint32_t* p, int idx, int lim) {
   asm volatile(
@@ -188,6 +217,11 @@ __device__ __forceinline__ void warp_load_bitonic(const KeyT* A, int X, const Ke
   const KeyT* pb = B + (kBlockItems - 1 - lane);     // C[32k+lane] = B[1023-32k-lane]
   const int xa = X - lane;                           // 32k + lane < X  <=>  32k < xa
   const int xb = kBlockItems - Y - lane;             // 32k + lane >= 1024 - Y  <=>  32k >= xb
+  if (X + Y == kBlockItems) {                        // full block: no pads, xa == xb
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = (32 * k < xa) ? pa[32 * k] : pb[-32 * k];
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < 32; ++k) {
     KeyT t = key_pad<KeyT>();

@@ -467,7 +467,7 @@ cudaError_t launch_seg_merge(void* a, void* b, const Desc* desc, const int* tota
                              const long long* table, int* dev_err, cudaStream_t s) {
   auto k = seg_merge_kernel<KeyT, WARPS>;
   const size_t bar_off = seg_merge_bar_off<KeyT, WARPS>(kmax);
-  const size_t smem = bar_off + 16;
+  const size_t smem = bar_off + 16 + kMergeCtlBytes;
   cudaError_t e = set_smem(k, smem, s);
   unsigned grid = 1;
   if (e == cudaSuccess) e = persistent_grid(k, WARPS * 32, smem, upper, &grid);
@@ -543,11 +543,11 @@ mms_status seg_prepare(mms_key_type kt, bool pairs, int tw, int kmax) {
   }
   if (e == cudaSuccess) {
     if (pairs || kt == MMS_KEY_U64) {
-      if (tw == 4) e = attr(seg_merge_kernel<uint64_t, 4>, seg_merge_bar_off<uint64_t, 4>(kmax) + 16);
-      if (tw == 2) e = attr(seg_merge_kernel<uint64_t, 2>, seg_merge_bar_off<uint64_t, 2>(kmax) + 16);
+      if (tw == 4) e = attr(seg_merge_kernel<uint64_t, 4>, seg_merge_bar_off<uint64_t, 4>(kmax) + 16 + kMergeCtlBytes);
+      if (tw == 2) e = attr(seg_merge_kernel<uint64_t, 2>, seg_merge_bar_off<uint64_t, 2>(kmax) + 16 + kMergeCtlBytes);
     } else {
-      if (tw == 8) e = attr(seg_merge_kernel<uint32_t, 8>, seg_merge_bar_off<uint32_t, 8>(kmax) + 16);
-      if (tw == 4) e = attr(seg_merge_kernel<uint32_t, 4>, seg_merge_bar_off<uint32_t, 4>(kmax) + 16);
+      if (tw == 8) e = attr(seg_merge_kernel<uint32_t, 8>, seg_merge_bar_off<uint32_t, 8>(kmax) + 16 + kMergeCtlBytes);
+      if (tw == 4) e = attr(seg_merge_kernel<uint32_t, 4>, seg_merge_bar_off<uint32_t, 4>(kmax) + 16 + kMergeCtlBytes);
     }
   }
   return e == cudaSuccess ? MMS_OK : seg_fail(MMS_ERR_CUDA, cudaGetErrorString(e));
