@@ -194,7 +194,7 @@ def aggregate_over_ranks(total_ms: float, keys_per_rank: int, steps: int, world:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ["merge_pass.cu", "mms_common.cuh", "mms_kernels.cuh"]:
+    for f in ["merge_pass.cu", "merge_tile.cuh", "mms_common.cuh", "mms_kernels.cuh"]:
         with open(os.path.join(ROOT, "paper_1702_07961_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
