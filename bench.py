@@ -48,12 +48,14 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=1 << 25)
-    p.add_argument("--workload", default="sort", choices=["sort", "batched", "serve"],
+    p.add_argument("--workload", default="sort", choices=["sort", "batched", "serve", "configs"],
                    help="sort: one 10^8-key array per step; batched: 20000 arrays of "
                         "log-uniform size in [2^8, 2^20] with uint32 payloads per step")
     p.add_argument("--arrays", type=int, default=20000)
     p.add_argument("--retune", action="store_true", help="batched: re-run the autotuner")
     p.add_argument("--requests", type=int, default=100, help="serve: requests per arrival-rate run")
+    p.add_argument("--max-swaps", type=float, default=1e8,
+                   help="configs: largest sortedness swap count r (10^9 takes minutes on the host)")
     return p.parse_args()
 
 
@@ -484,6 +486,121 @@ def run_serve(args):
     return 0
 
 
+def run_configs(args):
+    """The paper-shaped configurations beside the headline one: 2^20 uniform
+    keys; 10^8 keys by sortedness r (key-only and with index payloads); 2^28
+    interleaved stride-32 runs as u32 and u64; 2^28 N(0,1) floats with
+    duplicates, -0.0 and NaNs.  Each is sorted `steps` times through the C ABI
+    and checked against a closed form, the oracle, or order+multiset."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_1702_07961_gb300 as mms
+    import synth
+    dev = torch.device("cuda", 0)
+    results = []
+
+    def timed(work, src, ws, kt, vals=None, vsrc=None, steps=args.steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(args.warmup + steps):
+            work.copy_(src)
+            if vals is not None:
+                vals.copy_(vsrc)
+            if i >= args.warmup:
+                evs[i - args.warmup][0].record()
+            if vals is None:
+                mms.sort_keys(work, workspace=ws, kt=kt)
+            else:
+                mms.sort_pairs(work, vals, workspace=ws, kt=kt)
+            if i >= args.warmup:
+                evs[i - args.warmup][1].record()
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+    def add(name, n, ms, ok, kt, pairs=False, note=""):
+        plan = mms.plan(kt, n, pairs=pairs)
+        passes = 1 + len(plan)
+        kb = 8 if (pairs or kt == mms.KEY_U64) else 4
+        results.append({"config": name, "n": n, "ms": ms, "gkeys_per_s": n / ms / 1e6, "verified": bool(ok),
+                        "fanouts": plan, "passes": passes,
+                        "hbm_frac_whole_sort": passes * 2 * n * kb / (ms / 1e3) / 1e9 / 6787.6, "note": note})
+
+    # C1: 2^20 uniform u32, bit-exact against the oracle
+    n = 1 << 20
+    keys = synth.uniform(n, 1)
+    src = torch.from_numpy(keys.view(np.int32)).to(dev)
+    work = torch.empty_like(src)
+    ws = torch.zeros(mms.workspace_bytes(mms.KEY_U32, n), dtype=torch.uint8, device=dev)
+    ms = timed(work, src, ws, mms.KEY_U32)
+    ok = np.array_equal(work.cpu().numpy().view(np.uint32), oracle.sort(keys)[0])
+    add("C1 2^20 uniform u32", n, ms, ok, mms.KEY_U32, note="fits in L2")
+
+    # C2: 10^8 by sortedness, key-only and with the index payload (closed forms)
+    n = 10**8
+    iota = torch.arange(n, dtype=torch.int64, device=dev)
+    ws = torch.zeros(mms.workspace_bytes(mms.KEY_U32, n, True), dtype=torch.uint8, device=dev)
+    vsrc = torch.arange(n, dtype=torch.int32, device=dev)
+    vals = torch.empty_like(vsrc)
+    swaps = [0, 10**3, 10**5, 10**7, 10**8, 10**9]
+    for r in [x for x in swaps if x <= args.max_swaps] + ["permutation"]:
+        keys = synth.permutation(n, 1) if r == "permutation" else synth.sortedness(n, int(r), 2)
+        src = torch.from_numpy(keys.view(np.int32)).to(dev)
+        work = torch.empty_like(src)
+        for pairs in (False, True):
+            ms = timed(work, src, ws, mms.KEY_U32, vals if pairs else None, vsrc)
+            ok = bool(torch.equal(work.to(torch.int64) & 0xFFFFFFFF, iota))
+            if pairs:
+                inv = torch.empty(n, dtype=torch.int64, device=dev)
+                inv[src.to(torch.int64) & 0xFFFFFFFF] = iota
+                ok &= bool(torch.equal(vals.to(torch.int64), inv))
+                del inv
+            label = "fully random permutation" if r == "permutation" else f"sortedness r={int(r):.0e}"
+            add(f"C2 10^8 u32 {label}" + (" + index payload" if pairs else ""), n, ms, ok, mms.KEY_U32, pairs)
+        del src, work
+    del ws, vals, vsrc, iota
+    torch.cuda.empty_cache()
+
+    # C3: 2^28 interleaved stride-32 runs (u32, u64): sorted result is iota
+    n = 1 << 28
+    for dt, kt in ((np.uint32, mms.KEY_U32), (np.uint64, mms.KEY_U64)):
+        keys = synth.interleaved(n, 8, 32, dt)
+        src = torch.from_numpy(keys.view(np.int32 if dt == np.uint32 else np.int64)).to(dev)
+        work = torch.empty_like(src)
+        ws = torch.zeros(mms.workspace_bytes(kt, n), dtype=torch.uint8, device=dev)
+        ms = timed(work, src, ws, kt, steps=max(3, args.steps // 3))
+        want = torch.arange(n, dtype=torch.int64, device=dev)
+        if dt == np.uint64:
+            want = (want << 32) | want
+            ok = bool(torch.equal(work, want))
+        else:
+            ok = bool(torch.equal(work.to(torch.int64) & 0xFFFFFFFF, want))
+        add(f"C3 2^28 {np.dtype(dt).name} interleaved K=8 stride 32", n, ms, ok, kt)
+        del src, work, ws, want
+        torch.cuda.empty_cache()
+    # C3: 2^28 float32 N(0,1) with 1% duplicates, 0.1% -0.0, 0.01% NaN: totalOrder order + multiset
+    keys = synth.normal_f32(n, 3)
+    src = torch.from_numpy(keys).to(dev)
+    work = torch.empty_like(src)
+    ws = torch.zeros(mms.workspace_bytes(mms.KEY_F32, n), dtype=torch.uint8, device=dev)
+    ms = timed(work, src, ws, mms.KEY_F32, steps=max(3, args.steps // 3))
+    b = work.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    ordv = torch.where(b >= 2**31, b ^ 0xFFFFFFFF, b | 2**31)        # totalOrder on bit patterns
+    ok = bool(torch.all(ordv[1:] >= ordv[:-1]))
+    sb = src.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    mix = lambda x: ((x * 0x9E3779B97F4A7C15) ^ (x >> 7)) & 0xFFFFFFFFFFFF
+    ok &= bool(mix(b).sum() == mix(sb).sum()) and bool((b * b).sum() == (sb * sb).sum())
+    add("C3 2^28 f32 N(0,1) + dups, -0.0, NaN", n, ms, ok, mms.KEY_F32,
+        note="verified by totalOrder non-decreasing + multiset hash")
+    out = {"metric": "Gkeys/s per configuration", "unit": "Gkeys/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "dtype": "u32/u64/f32", "data": "synthetic", "results": results,
+           "all_verified": all(r["verified"] for r in results)}
+    print(json.dumps(out), flush=True)
+    return 0 if out["all_verified"] else 1
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -492,6 +609,8 @@ def main():
         return run_batched(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "configs":
+        return run_configs(args)
     import numpy as np
     import torch
 
