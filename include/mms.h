@@ -60,7 +60,9 @@ typedef struct {
                         i < num_events.  Lets a caller time every step of the real call. */
   int tile_items;    /* base-case / merge tile: 0 = mms_tile_items(kt); else 4096 or 8192
                         for 4-byte keys, 2048 or 4096 for 8-byte keys */
-  int reserved[3];
+  int merge_tile_items; /* output tile of the merge rounds: 0 = tile_items; else a multiple
+                        of 1024 from 4096 (2048 for 8-byte keys) up to tile_items */
+  int reserved[2];
 } mms_options;
 
 /* Bytes of workspace mms_sort_keys / mms_sort_pairs need for n keys: one

@@ -39,7 +39,7 @@ class MMSError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("fanout", ctypes.c_int), ("num_events", ctypes.c_int),
                 ("events", ctypes.POINTER(ctypes.c_void_p)), ("tile_items", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("merge_tile_items", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class _SegOptions(ctypes.Structure):
@@ -135,10 +135,11 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
-def _opts(fanout: int, events=None, stream=None, tile_items: int = 0):
+def _opts(fanout: int, events=None, stream=None, tile_items: int = 0, merge_tile_items: int = 0):
     o = _Options()
     o.fanout = int(fanout)
     o.tile_items = int(tile_items)
+    o.merge_tile_items = int(merge_tile_items)
     if events:
         for e in events:
             if not e.cuda_event:          # torch creates the CUDA event on first record
@@ -170,7 +171,7 @@ def plan(kt: int, n: int, fanout: int = 0, tile_items: int = 0, pairs: bool = Fa
 
 
 def sort_keys(keys, fanout: int = 0, workspace=None, stream=None, kt: int | None = None, events=None,
-              tile_items: int = 0):
+              tile_items: int = 0, merge_tile_items: int = 0):
     """Sorts a contiguous CUDA tensor of keys in place; returns it.
 
     ``events``: optional list of ``torch.cuda.Event(enable_timing=True)``; the
@@ -180,7 +181,7 @@ def sort_keys(keys, fanout: int = 0, workspace=None, stream=None, kt: int | None
     kt = key_type_of(keys) if kt is None else kt
     n = keys.numel()
     ws_ptr, ws_len = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
-    o = _opts(fanout, events, stream, tile_items)
+    o = _opts(fanout, events, stream, tile_items, merge_tile_items)
     _check(load().mms_sort_keys_ex(kt, _ptr(keys), n, ws_ptr, ws_len, _stream_handle(stream), ctypes.byref(o)))
     return keys
 

@@ -97,6 +97,25 @@ int plan_rounds(int key_bytes, size_t n, const mms_options* opt, int* K, int max
   return rounds;
 }
 
+// Output tile of the merge rounds (a multiple of 1024, at most the base-case
+// tile T).  The default is T.  A smaller tile can keep every tree level within
+// one block per warp (with K = 4 on 8 warps an 8192-item tile's first level
+// has 9 blocks in general, a 7168-item tile's at most 8), but on GB300 the
+// extra tiles cost more than that saves (10^8 u32, K = 4: 0.325 ms per pass
+// at 7168 against 0.313 ms at 8192, splitters 0.54 ms against 0.47 ms); the
+// caller's mms_options.merge_tile_items selects one.  The workspace's pivot
+// table holds n / S_min + 1 rows; a tile that would need more falls back to T.
+long long merge_tile_for(int key_bytes, int tw, int K, const mms_options* opt, size_t n,
+                         long long run_len) {
+  const long long T = 1024ll * tw;
+  long long S = T;
+  if (opt && opt->merge_tile_items > 0) S = opt->merge_tile_items;
+  const long long S_min = key_bytes == 8 ? 2048 : 4096;
+  const long long cap = ((long long)n + S_min - 1) / S_min + 1;
+  if (mms::num_tiles(S, (long long)n, run_len, K) + 1 > cap) S = T;
+  return S;
+}
+
 mms_status check_launch(cudaError_t e, const char* where) {
   return e == cudaSuccess ? MMS_OK : cuda_fail(e, where);
 }
@@ -172,6 +191,10 @@ mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws,
     return fail(MMS_ERR_INVALID_ARG, "tile_items must be 0, 4096/8192 (4-byte keys) or 2048/4096 (8-byte keys)%s");
   const int tw = tile_warps_for(kb, opt);
   const long long S = 1024ll * tw;
+  if (opt && opt->merge_tile_items != 0 &&
+      (opt->merge_tile_items % 1024 != 0 || opt->merge_tile_items < (kb == 8 ? 2048 : 4096) ||
+       opt->merge_tile_items > S))
+    return fail(MMS_ERR_INVALID_ARG, "merge_tile_items must be 0 or a multiple of 1024 from the smallest tile up to tile_items%s");
   const WsLayout L = ws_layout(kt, n, 0);
   cudaStream_t s = (cudaStream_t)stream;
   bool owned = false;
@@ -209,10 +232,11 @@ mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws,
   mark();
   long long run_len = S;
   for (int r = 0; r < rounds && st == MMS_OK; ++r) {
-    st = check_launch(mms::launch_splitter(kb, S, cur, (long long)n, run_len, K[r], table, s), "splitter");
+    const long long Sm = merge_tile_for(kb, tw, K[r], opt, n, run_len);
+    st = check_launch(mms::launch_splitter(kb, Sm, cur, (long long)n, run_len, K[r], table, s), "splitter");
     mark();
     if (st != MMS_OK) break;
-    st = check_launch(mms::launch_merge_pass(kb, tw, is_f32 && r == rounds - 1, cur, other,
+    st = check_launch(mms::launch_merge_pass(kb, tw, Sm, is_f32 && r == rounds - 1, cur, other,
                                              (long long)n, run_len, K[r], table, dev_err, s),
                       "merge_pass");
     mark();
@@ -278,7 +302,7 @@ static mms_status pairs32_run(bool is_f32, void* d_keys, uint32_t* d_values, siz
     st = check_launch(mms::launch_splitter(8, S, comp[cur], (long long)n, run_len, K[r], table, s), "splitter");
     mark();
     if (st != MMS_OK) break;
-    st = check_launch(mms::launch_merge_pass(8, tw, false, comp[cur], comp[1 - cur], (long long)n,
+    st = check_launch(mms::launch_merge_pass(8, tw, S, false, comp[cur], comp[1 - cur], (long long)n,
                                              run_len, K[r], table, dev_err, s), "merge_pass");
     mark();
     cur = 1 - cur;
@@ -413,7 +437,8 @@ mms_status mms_merge_pass(mms_key_type kt, const void* d_in, void* d_out, size_t
   if (a < b + n * kb && b < a + n * kb) return fail(MMS_ERR_INVALID_ARG, "input and output overlap%s");
   if (d_ws && ws_bytes < kStatusBytes) return fail(MMS_ERR_INVALID_ARG, "workspace too small%s");
   int* dev_err = d_ws ? static_cast<int*>(d_ws) : nullptr;
-  return check_launch(mms::launch_merge_pass((int)kb, mms::default_tile_warps((int)kb), false, d_in,
+  return check_launch(mms::launch_merge_pass((int)kb, mms::default_tile_warps((int)kb),
+                                             1024ll * mms::default_tile_warps((int)kb), false, d_in,
                                              d_out, (long long)n,
                                              (long long)run_len, K,
                                              reinterpret_cast<const long long*>(d_table), dev_err,

@@ -64,8 +64,9 @@ inline size_t merge_pass_smem_bytes_impl(int key_bytes, int warps, int K) {
   return 0;
 }
 
-// Merges output tile j of group g of `in` (n items in sorted runs of run_len,
-// K runs per group) into `out`: the CTA body of a merge round.  lo_row and
+// Merges output tile j (of S items, a multiple of 1024 and at most
+// 1024 * WARPS) of group g of `in` (n items in sorted runs of run_len, K runs
+// per group) into `out`: the CTA body of a merge round.  lo_row and
 // hi_row are the pivot rows of the tile's start and end (read only when the
 // tile is not its group's first / last).  `bar` is an initialised mbarrier of
 // this CTA whose next phase completes with parity `phase`.  `xout` undoes the
@@ -78,10 +79,9 @@ __device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __
                                            long long j, const long long* __restrict__ lo_row,
                                            const long long* __restrict__ hi_row, bool xout,
                                            int* dev_err, unsigned char* smem_raw, uint64_t* bar,
-                                           unsigned phase) {
+                                           unsigned phase, int S) {
   using G = MergeGeom<KeyT, WARPS>;
   constexpr int E = G::E;
-  constexpr int S = G::S;
   const int cap = G::cap(K);
   KeyT* bufX = reinterpret_cast<KeyT*>(smem_raw);
   KeyT* bufY = bufX + cap;
@@ -115,7 +115,7 @@ __device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     const bool bad = __any_sync(0xffffffffu, bad_seg) || sum != want || K > kMaxFanout || K < 2 ||
-                     (smem_u32addr(smem_raw) & 1023u) != 0;
+                     S > G::S || S < kBlockItems || (smem_u32addr(smem_raw) & 1023u) != 0;
     if (lane == 0) {
       ctl[kCtlNodeFields * 32 + 2] = (int)want;
       ctl[kCtlNodeFields * 32 + 3] = bad ? 1 : 0;

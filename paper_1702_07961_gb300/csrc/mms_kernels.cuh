@@ -68,21 +68,26 @@ cudaError_t launch_u64_pairs_final(const void* kcopy, const void* vcopy, const v
 cudaError_t launch_splitter(int key_bytes, long long S, const void* in, long long n,
                             long long run_len, int K, long long* table, cudaStream_t s);
 
-// One K-way merge round driven by the splitter table.
-cudaError_t launch_merge_pass(int key_bytes, int tile_warps, bool xout, const void* in, void* out,
-                              long long n, long long run_len, int K, const long long* table,
-                              int* dev_err, cudaStream_t s);
+// One K-way merge round driven by the splitter table; output tiles of S
+// items (a multiple of 1024, at most 1024 * tile_warps).
+cudaError_t launch_merge_pass(int key_bytes, int tile_warps, long long S, bool xout, const void* in,
+                              void* out, long long n, long long run_len, int K,
+                              const long long* table, int* dev_err, cudaStream_t s);
 
 // Records the detail message mms_last_error_detail() returns on this thread.
 void set_error_detail(const char* msg);
 
 // Output tiles of a round: every group of K runs (K * run_len items, the last
-// group possibly short) is cut into tiles of S items.
+// group possibly short) is cut into tiles of S items, the last tile of every
+// group possibly short.
+__host__ __device__ inline long long tiles_per_group(long long S, long long run_len, int K) {
+  return (run_len * K + S - 1) / S;
+}
 __host__ __device__ inline long long num_tiles(long long S, long long n, long long run_len, int K) {
   const long long G = run_len * K;
   const long long full = n / G;
   const long long rest = n - full * G;
-  return full * (G / S) + (rest + S - 1) / S;
+  return full * tiles_per_group(S, run_len, K) + (rest + S - 1) / S;
 }
 
 }  // namespace mms

@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
     if (!merge_tile<KeyT, WARPS>(in, out, (long long)d.n, run_len, K, idx / tpg, idx % tpg,
                                  table + (long long)t * kRowStride,
                                  table + (long long)(t + 1) * kRowStride,
-                                 is_f32 && ((d.w >> 28) & 1u), dev_err, smem_raw, bar, phase))
+                                 is_f32 && ((d.w >> 28) & 1u), dev_err, smem_raw, bar, phase, S))
       return;
     phase ^= 1u;
   }

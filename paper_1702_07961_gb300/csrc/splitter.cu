@@ -17,7 +17,7 @@ cudaError_t launch_splitter(int key_bytes, long long S, const void* in, long lon
                             long long run_len, int K, long long* table, cudaStream_t s) {
   const long long ntiles = num_tiles(S, n, run_len, K);
   if (ntiles <= 0) return cudaSuccess;
-  const long long tpg = run_len * K / S;
+  const long long tpg = tiles_per_group(S, run_len, K);
   const unsigned grid = (unsigned)((ntiles + 3) / 4);
   if (key_bytes == 4)
     splitter_kernel<uint32_t><<<grid, 128, 0, s>>>(static_cast<const uint32_t*>(in), n, run_len, K,

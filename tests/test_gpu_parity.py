@@ -373,3 +373,15 @@ def test_bad_tile_width_is_rejected(gpu):
     t = to_dev(synth.uniform(10000, 1, np.uint32))
     with pytest.raises(gpu.MMSError):
         gpu.sort_keys(t, kt=gpu.KEY_U32, tile_items=2048)
+
+
+@pytest.mark.parametrize("fanout,merge_tile", [(4, 7168), (4, 4096), (8, 5120), (2, 6144), (3, 7168), (4, 8192)])
+def test_sort_merge_tile_sizes(gpu, fanout, merge_tile):
+    """Merge output tiles smaller than the base-case run (groups then end in a
+    short tile): any multiple of 1024 gives the same bits."""
+    n = 8192 * 37 + 5000
+    keys = synth.uniform(n, fanout * 31 + merge_tile, np.uint32) % np.uint32(50000)
+    want, _ = oracle.sort(keys)
+    t = to_dev(keys)
+    gpu.sort_keys(t, fanout=fanout, kt=gpu.KEY_U32, merge_tile_items=merge_tile)
+    assert_bits_equal(to_host(t, np.uint32), want)
