@@ -64,96 +64,76 @@ inline size_t merge_pass_smem_bytes_impl(int key_bytes, int warps, int K) {
   return 0;
 }
 
-// Merges output tile j (of S items, a multiple of 1024 and at most
-// 1024 * WARPS) of group g of `in` (n items in sorted runs of run_len, K runs
-// per group) into `out`: the CTA body of a merge round.  lo_row and
-// hi_row are the pivot rows of the tile's start and end (read only when the
-// tile is not its group's first / last).  `bar` is an initialised mbarrier of
-// this CTA whose next phase completes with parity `phase`.  `xout` undoes the
-// float transform on the tile's last level.  Returns false, with the error
-// recorded, when the CTA must stop (a pivot row fails its check or the
-// staging wait ran out); the decision is uniform over the CTA.
+// Plans output tile j of group g and stages its segments into `stage`: one
+// warp, one lane per run and one per merge-tree node.  Starts the bulk copies
+// on `bar`, loads the ragged ends, and writes the node table and the scalars
+// (levels, nodes, tile size, error) into `ctl`; the caller's CTA barrier
+// publishes the ragged ends and the table, the barrier's phase the copies.
+// On a pivot row that fails its check, ctl's error scalar is set and nothing
+// is staged.
 template <typename KeyT, int WARPS>
-__device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __restrict__ out,
-                                           long long n, long long run_len, int K, long long g,
-                                           long long j, const long long* __restrict__ lo_row,
-                                           const long long* __restrict__ hi_row, bool xout,
-                                           int* dev_err, unsigned char* smem_raw, uint64_t* bar,
-                                           unsigned phase, int S) {
+__device__ __forceinline__ void merge_plan_warp(const KeyT* __restrict__ in, long long n,
+                                                long long run_len, int K, long long g,
+                                                long long j, const long long* __restrict__ lo_row,
+                                                const long long* __restrict__ hi_row, int S,
+                                                KeyT* stage, int* ctl, uint64_t* bar, int lane) {
   using G = MergeGeom<KeyT, WARPS>;
   constexpr int E = G::E;
-  const int cap = G::cap(K);
-  KeyT* bufX = reinterpret_cast<KeyT*>(smem_raw);
-  KeyT* bufY = bufX + cap;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
   const long long gstart = g * run_len * K;
-  int* ctl = reinterpret_cast<int*>(bar + 2);          // node table and scalars (see above)
-
-  // Every thread is past the previous tile (whose store has read its shared
-  // memory) before the staging copies overwrite the buffer.
-  __syncthreads();
-  if (warp == 0) {
-    // Warp 0 alone plans the tile: one lane per run, one lane per tree node.
-    const long long grest = n - gstart;
-    const long long gsize = grest < run_len * K ? grest : run_len * K;
-    const long long tiles_here = (gsize + S - 1) / S;
-    const bool act = lane < K;
-    const long long rstart = gstart + (long long)lane * run_len;
-    long long rlen = n - rstart;
-    rlen = rlen < 0 ? 0 : (rlen > run_len ? run_len : rlen);
-    long long lo = 0, hi = 0;
-    if (act) {
-      lo = (j == 0) ? 0 : lo_row[lane];
-      hi = (j + 1 < tiles_here) ? hi_row[lane] : rlen;
-    }
-    // The pivot rows must describe segments inside their runs whose lengths
-    // sum to this tile's size; anything else would overrun the staging buffer.
-    const long long want = (gsize - j * S) < S ? (gsize - j * S) : S;
-    const bool bad_seg = act && (lo < 0 || hi < lo || hi > rlen);
-    long long sum = act ? hi - lo : 0;
+  const long long grest = n - gstart;
+  const long long gsize = grest < run_len * K ? grest : run_len * K;
+  const long long tiles_here = (gsize + S - 1) / S;
+  const bool act = lane < K;
+  const long long rstart = gstart + (long long)lane * run_len;
+  long long rlen = n - rstart;
+  rlen = rlen < 0 ? 0 : (rlen > run_len ? run_len : rlen);
+  long long lo = 0, hi = 0;
+  if (act) {
+    lo = (j == 0) ? 0 : lo_row[lane];
+    hi = (j + 1 < tiles_here) ? hi_row[lane] : rlen;
+  }
+  // The pivot rows must describe segments inside their runs whose lengths
+  // sum to this tile's size; anything else would overrun the staging buffer.
+  const long long want = (gsize - j * S) < S ? (gsize - j * S) : S;
+  const bool bad_seg = act && (lo < 0 || hi < lo || hi > rlen);
+  long long sum = act ? hi - lo : 0;
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    const bool bad = __any_sync(0xffffffffu, bad_seg) || sum != want || K > kMaxFanout || K < 2 ||
-                     S > G::S || S < kBlockItems || (smem_u32addr(smem_raw) & 1023u) != 0;
-    if (lane == 0) {
-      ctl[kCtlNodeFields * 32 + 2] = (int)want;
-      ctl[kCtlNodeFields * 32 + 3] = bad ? 1 : 0;
-    }
-    if (!bad) {
-      const long long gsrc = rstart + lo;              // first item, index into `in`
-      const int len = act ? (int)(hi - lo) : 0;
-      // `in` itself may sit off the 16-byte grid (a segment of a batch): the
-      // bulk copies align on absolute addresses.
-      const int in_mis = (int)(((uintptr_t)in / sizeof(KeyT)) & (E - 1));
-      const int head = act ? (int)((in_mis + gsrc) % E) : 0;   // items copied before the segment
-      const int span = (head + len + E - 1) / E * E + G::kSlack;   // staged span + transpose slack
-      int incl = span;
-      int lincl = len;
+  for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  const bool bad = __any_sync(0xffffffffu, bad_seg) || sum != want || K > kMaxFanout || K < 2 ||
+                   S > G::S || S < kBlockItems || (smem_u32addr(stage) & 15u) != 0;
+  if (lane == 0) {
+    ctl[kCtlNodeFields * 32 + 2] = (int)want;
+    ctl[kCtlNodeFields * 32 + 3] = bad ? 1 : 0;
+  }
+  if (!bad) {
+    const long long gsrc = rstart + lo;              // first item, index into `in`
+    const int len = act ? (int)(hi - lo) : 0;
+    // `in` itself may sit off the 16-byte grid (a segment of a batch): the
+    // bulk copies align on absolute addresses.
+    const int in_mis = (int)(((uintptr_t)in / sizeof(KeyT)) & (E - 1));
+    const int head = act ? (int)((in_mis + gsrc) % E) : 0;   // items copied before the segment
+    const int span = (head + len + E - 1) / E * E + G::kSlack;   // staged span + transpose slack
+    int incl = span;
+    int lincl = len;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int x = __shfl_up_sync(0xffffffffu, incl, o);
-        const int y = __shfl_up_sync(0xffffffffu, lincl, o);
-        if (lane >= o) {
-          incl += x;
-          lincl += y;
-        }
+    for (int o = 1; o < 32; o <<= 1) {
+      const int x = __shfl_up_sync(0xffffffffu, incl, o);
+      const int y = __shfl_up_sync(0xffffffffu, lincl, o);
+      if (lane >= o) {
+        incl += x;
+        lincl += y;
       }
-      const int R = incl - span;                       // span start of segment `lane`
-      const int lpre = lincl - len;                    // items in segments before `lane`
-      // Bulk part: from gsrc - head to the last 16-byte boundary (of absolute
-      // addresses) inside the segment; the rest by plain loads.
-      const long long bulk_lo = gsrc - head;
-      const long long bulk_hi = (in_mis + gsrc + len) / E * E - in_mis;
-      const unsigned bulk_bytes =
-          (act && bulk_hi > bulk_lo) ? (unsigned)((bulk_hi - bulk_lo) * sizeof(KeyT)) : 0u;
-      unsigned total = bulk_bytes;
-#pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
-      if (lane == 0) mbar_arrive_expect_tx(bar, total);
-      __syncwarp();
-      if (bulk_bytes) bulk_g2s(bufX + R, in + bulk_lo, bulk_bytes, bar);
-      // Ragged ends, one segment at a time, consecutive lanes -> consecutive words.
+    }
+    const int R = incl - span;                       // span start of segment `lane`
+    const int lpre = lincl - len;                    // items in segments before `lane`
+    // Bulk part: from gsrc - head to the last 16-byte boundary (of absolute
+    // addresses) inside the segment; the rest by plain loads.
+    const long long bulk_lo = gsrc - head;
+    const long long bulk_hi = (in_mis + gsrc + len) / E * E - in_mis;
+    const unsigned bulk_bytes =
+        (act && bulk_hi > bulk_lo) ? (unsigned)((bulk_hi - bulk_lo) * sizeof(KeyT)) : 0u;
+    // Ragged ends, one segment at a time, consecutive lanes -> consecutive words.
+    auto ragged = [&]() {
       for (int r = 0; r < K; ++r) {
         const long long s_src = __shfl_sync(0xffffffffu, gsrc, r);
         const int s_len = __shfl_sync(0xffffffffu, len, r);
@@ -162,69 +142,82 @@ __device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __
         const long long s_blo = __shfl_sync(0xffffffffu, bulk_lo, r);
         const long long from = (s_bhi > s_blo) ? s_bhi : s_src;   // first item not bulk-copied
         const long long e = from + lane;
-        if (e < s_src + s_len) bufX[s_off + (int)(e - s_src)] = in[e];
+        if (e < s_src + s_len) stage[s_off + (int)(e - s_src)] = in[e];
       }
-
-      // Merge-tree nodes, one per lane, in level order: node (level l >= 1,
-      // pair q) merges child A = segments [q*2^l, q*2^l + 2^(l-1)) and child
-      // B = the rest of [q*2^l, (q+1)*2^l) (clipped to K).
-      int nl = 0, nnodes = 0, c_level = 0, c_pair = 0;
-      {
-        int cnt = K, idx = 0;
-        for (int l = 1; cnt > 1; ++l) {
-          const int pairs = (cnt + 1) >> 1;
-          if (lane >= idx && lane < idx + pairs) {
-            c_level = l;
-            c_pair = lane - idx;
-          }
-          idx += pairs;
-          cnt = pairs;
-          nl = l;
-        }
-        nnodes = idx;
-      }
-      const bool is_node = lane < nnodes;
-      const int first = c_pair << c_level;             // first segment of the node
-      const int mid = first + (1 << (c_level > 0 ? c_level - 1 : 0));
-      const int last = first + (1 << c_level);
-      auto seg_pre = [&](int sg) {                     // items in segments [0, sg)
-        const int ss = sg < K ? sg : K;
-        const int v = __shfl_sync(0xffffffffu, lpre, ss & 31);
-        return ss >= K ? (int)want : v;
-      };
-      const int pf = seg_pre(first), pm = seg_pre(mid), pl = seg_pre(last);
-      const int rf = __shfl_sync(0xffffffffu, R, first & 31);
-      const int hf = __shfl_sync(0xffffffffu, head, first & 31);
-      const int rm = __shfl_sync(0xffffffffu, R, mid & 31);
-      const int hm = __shfl_sync(0xffffffffu, head, mid & 31);
-      const int lenA = is_node ? pm - pf : 0;
-      const int lenB = is_node ? pl - pm : 0;
-      const int nb = (lenA + lenB + kBlockItems - 1) / kBlockItems;
-      int fst = nb;
+    };
+    unsigned total = bulk_bytes;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int x = __shfl_up_sync(0xffffffffu, fst, o);
-        if (lane >= o) fst += x;
+    for (int o = 16; o >= 1; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+    if (lane == 0) mbar_arrive_expect_tx(bar, total);
+    __syncwarp();
+    if (bulk_bytes) bulk_g2s(stage + R, in + bulk_lo, bulk_bytes, bar);
+    ragged();
+    // Merge-tree nodes, one per lane, in level order: node (level l >= 1,
+    // pair q) merges child A = segments [q*2^l, q*2^l + 2^(l-1)) and child
+    // B = the rest of [q*2^l, (q+1)*2^l) (clipped to K).
+    int nl = 0, nnodes = 0, c_level = 0, c_pair = 0;
+    {
+      int cnt = K, idx = 0;
+      for (int l = 1; cnt > 1; ++l) {
+        const int pairs = (cnt + 1) >> 1;
+        if (lane >= idx && lane < idx + pairs) {
+          c_level = l;
+          c_pair = lane - idx;
+        }
+        idx += pairs;
+        cnt = pairs;
+        nl = l;
       }
-      ctl[0 * 32 + lane] = lenA;
-      ctl[1 * 32 + lane] = lenB;
-      ctl[2 * 32 + lane] = (c_level == 1) ? rf + hf : rf;                     // staged segment
-      ctl[3 * 32 + lane] = (mid < K) ? ((c_level == 1) ? rm + hm : rm) : 0;   // vs. child output
-      ctl[4 * 32 + lane] = rf;                                                // output span
-      ctl[5 * 32 + lane] = fst - nb;                                          // first block
-      ctl[6 * 32 + lane] = nb;
-      ctl[7 * 32 + lane] = is_node ? c_level : 0;
-      if (lane == 0) {
-        ctl[kCtlNodeFields * 32 + 0] = nl;
-        ctl[kCtlNodeFields * 32 + 1] = nnodes;
-      }
+      nnodes = idx;
+    }
+    const bool is_node = lane < nnodes;
+    const int first = c_pair << c_level;             // first segment of the node
+    const int mid = first + (1 << (c_level > 0 ? c_level - 1 : 0));
+    const int last = first + (1 << c_level);
+    auto seg_pre = [&](int sg) {                     // items in segments [0, sg)
+      const int ss = sg < K ? sg : K;
+      const int v = __shfl_sync(0xffffffffu, lpre, ss & 31);
+      return ss >= K ? (int)want : v;
+    };
+    const int pf = seg_pre(first), pm = seg_pre(mid), pl = seg_pre(last);
+    const int rf = __shfl_sync(0xffffffffu, R, first & 31);
+    const int hf = __shfl_sync(0xffffffffu, head, first & 31);
+    const int rm = __shfl_sync(0xffffffffu, R, mid & 31);
+    const int hm = __shfl_sync(0xffffffffu, head, mid & 31);
+    const int lenA = is_node ? pm - pf : 0;
+    const int lenB = is_node ? pl - pm : 0;
+    const int nb = (lenA + lenB + kBlockItems - 1) / kBlockItems;
+    int fst = nb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int x = __shfl_up_sync(0xffffffffu, fst, o);
+      if (lane >= o) fst += x;
+    }
+    ctl[0 * 32 + lane] = lenA;
+    ctl[1 * 32 + lane] = lenB;
+    ctl[2 * 32 + lane] = (c_level == 1) ? rf + hf : rf;                     // staged segment
+    ctl[3 * 32 + lane] = (mid < K) ? ((c_level == 1) ? rm + hm : rm) : 0;   // vs. child output
+    ctl[4 * 32 + lane] = rf;                                                // output span
+    ctl[5 * 32 + lane] = fst - nb;                                          // first block
+    ctl[6 * 32 + lane] = nb;
+    ctl[7 * 32 + lane] = is_node ? c_level : 0;
+    if (lane == 0) {
+      ctl[kCtlNodeFields * 32 + 0] = nl;
+      ctl[kCtlNodeFields * 32 + 1] = nnodes;
     }
   }
-  __syncthreads();
-  if (ctl[kCtlNodeFields * 32 + 3]) {
-    if (threadIdx.x == 0) set_device_error(dev_err, kDevErrInternal);
-    return false;                                      // uniform over the CTA
-  }
+}
+
+// Merges a staged tile level by level and writes it to dstg: run by the
+// WARPS merging warps (threads 0 .. 32 * WARPS - 1).  bufX holds the staged
+// segments, bufY is the other level buffer; `ctl` is the tile's node table.
+// sync() is a barrier over exactly the merging warps; the caller has made the
+// staged data and the table visible to them.
+template <typename KeyT, int WARPS, typename Sync>
+__device__ __forceinline__ void merge_levels(KeyT* bufX, KeyT* bufY, const int* ctl,
+                                             KeyT* __restrict__ dstg, bool xout, Sync sync) {
+  constexpr int E = Vec16<KeyT>::E;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nl = ctl[kCtlNodeFields * 32 + 0];
   const int nnodes = ctl[kCtlNodeFields * 32 + 1];
   const long long want = ctl[kCtlNodeFields * 32 + 2];
@@ -233,15 +226,6 @@ __device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __
   const int c_offA = ctl[2 * 32 + lane], c_offB = ctl[3 * 32 + lane];
   const int c_out = ctl[4 * 32 + lane], c_first = ctl[5 * 32 + lane];
   const int c_nb = ctl[6 * 32 + lane], c_level = ctl[7 * 32 + lane];
-
-  // One thread polls the staging barrier; the others wait at the CTA barrier
-  // (no issue slots spent polling), which also orders the staged data and the
-  // ragged-end stores before every warp's reads.
-  const bool ok = (threadIdx.x == 0) ? mbar_wait_bounded(bar, phase) : true;
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) set_device_error(dev_err, kDevErrTimeout);
-    return false;
-  }
 
   // Level by level: the blocks of every node of level lv are dealt to the
   // warps round-robin; a barrier ends the level.
@@ -273,17 +257,60 @@ __device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __
                              xout && lv == nl);
       __syncwarp();
     }
-    __syncthreads();
+    sync();
   }
   // The root node's output is the tile, at span start 0 of the last level's buffer.
   const KeyT* res = (nl & 1) ? bufY : bufX;
   const int m = (int)want;
-  KeyT* dstg = out + gstart + j * S;
   const int body = (((uintptr_t)dstg & 15u) == 0) ? m / E * E : 0;   // off-grid: plain stores
   fence_proxy_async_smem();
-  __syncthreads();
+  sync();
   if (threadIdx.x == 0 && body > 0) bulk_s2g_and_wait(dstg, res, (unsigned)(body * sizeof(KeyT)));
-  for (int i = body + (int)threadIdx.x; i < m; i += blockDim.x) dstg[i] = res[i];
+  for (int i = body + (int)threadIdx.x; i < m; i += WARPS * 32) dstg[i] = res[i];
+}
+
+// Merges output tile j (of S items, a multiple of 1024 and at most
+// 1024 * WARPS) of group g of `in` (n items in sorted runs of run_len, K runs
+// per group) into `out`: the CTA body of a merge round, one tile at a time.
+// lo_row and hi_row are the pivot rows of the tile's start and end (read only
+// when the tile is not its group's first / last).  `bar` is an initialised
+// mbarrier of this CTA whose next phase completes with parity `phase`.
+// `xout` undoes the float transform on the tile's last level.  Returns false,
+// with the error recorded, when the CTA must stop (a pivot row fails its
+// check or the staging wait ran out); the decision is uniform over the CTA.
+template <typename KeyT, int WARPS>
+__device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __restrict__ out,
+                                           long long n, long long run_len, int K, long long g,
+                                           long long j, const long long* __restrict__ lo_row,
+                                           const long long* __restrict__ hi_row, bool xout,
+                                           int* dev_err, unsigned char* smem_raw, uint64_t* bar,
+                                           unsigned phase, int S) {
+  using G = MergeGeom<KeyT, WARPS>;
+  const int cap = G::cap(K);
+  KeyT* bufX = reinterpret_cast<KeyT*>(smem_raw);
+  KeyT* bufY = bufX + cap;
+  int* ctl = reinterpret_cast<int*>(bar + 2);          // node table and scalars (see above)
+  // Every thread is past the previous tile (whose store has read its shared
+  // memory) before the staging copies overwrite the buffer.
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0)
+    merge_plan_warp<KeyT, WARPS>(in, n, run_len, K, g, j, lo_row, hi_row, S, bufX, ctl, bar,
+                                        threadIdx.x & 31);
+  __syncthreads();
+  if (ctl[kCtlNodeFields * 32 + 3] || (smem_u32addr(smem_raw) & 1023u) != 0) {
+    if (threadIdx.x == 0) set_device_error(dev_err, kDevErrInternal);
+    return false;                                      // uniform over the CTA
+  }
+  // One thread polls the staging barrier; the others wait at the CTA barrier
+  // (no issue slots spent polling), which also orders the staged data and the
+  // ragged-end stores before every warp's reads.
+  const bool ok = (threadIdx.x == 0) ? mbar_wait_bounded(bar, phase) : true;
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) set_device_error(dev_err, kDevErrTimeout);
+    return false;
+  }
+  merge_levels<KeyT, WARPS>(bufX, bufY, ctl, out + g * run_len * K + j * S, xout,
+                            []() { __syncthreads(); });
   return true;
 }
 
