@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=1 << 25)
-    p.add_argument("--workload", default="sort", choices=["sort", "batched", "serve", "configs"],
+    p.add_argument("--workload", default="sort", choices=["sort", "batched", "serve", "configs", "sweep"],
                    help="sort: one 10^8-key array per step; batched: 20000 arrays of "
                         "log-uniform size in [2^8, 2^20] with uint32 payloads per step")
     p.add_argument("--arrays", type=int, default=20000)
@@ -601,6 +601,66 @@ def run_configs(args):
     return 0 if out["all_verified"] else 1
 
 
+def run_sweep(args):
+    """Fanout K x size N sweep (the paper's Sec. 6.2 tuning and Sec. 6.3 size
+    experiments, on GB300): uniform random u32 and u64 keys from a seeded
+    device generator, every K in {2, 4, 8, 16, 32}, sizes 2^20 .. 2^28.  Each
+    result is checked for non-decreasing order and an unchanged key sum."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1702_07961_gb300 as mms
+    dev = torch.device("cuda", 0)
+    rows = []
+    for kt, name in ((mms.KEY_U32, "u32"), (mms.KEY_U64, "u64")):
+        sizes = [1 << 20, 1 << 22, 1 << 24, 1 << 26, 10**8] + ([1 << 28] if kt == mms.KEY_U32 else [])
+        for n in sizes:
+            g = torch.Generator(device=dev).manual_seed(n + kt)
+            if kt == mms.KEY_U32:
+                src = torch.randint(-2**31, 2**31 - 1, (n,), dtype=torch.int32, device=dev, generator=g)
+            else:
+                src = torch.randint(-2**63, 2**63 - 1, (n,), dtype=torch.int64, device=dev, generator=g)
+            work = torch.empty_like(src)
+            ws = torch.zeros(mms.workspace_bytes(kt, n), dtype=torch.uint8, device=dev)
+            ref_sum = int(src.to(torch.int64).sum().item()) if kt == mms.KEY_U32 else None
+            for K in (2, 4, 8, 16, 32):
+                plan = mms.plan(kt, n, K)
+                n_ev = 2 + 2 * len(plan)
+                steps = max(3, min(args.steps, 10))
+                evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(steps)]
+                for i in range(args.warmup + steps):
+                    work.copy_(src)
+                    mms.sort_keys(work, fanout=K, workspace=ws, kt=kt,
+                                  events=evs[i - args.warmup] if i >= args.warmup else None)
+                torch.cuda.synchronize()
+                if kt == mms.KEY_U32:
+                    w = work.to(torch.int64) & 0xFFFFFFFF
+                    ok = bool(torch.all(w[1:] >= w[:-1])) and int(work.to(torch.int64).sum().item()) == ref_sum
+                else:
+                    hi = (work >> 32) & 0xFFFFFFFF
+                    lo = work & 0xFFFFFFFF
+                    ok = bool(torch.all((hi[1:] > hi[:-1]) | ((hi[1:] == hi[:-1]) & (lo[1:] >= lo[:-1]))))
+                    ok &= bool(torch.equal(torch.sort(work).values, torch.sort(src).values))
+                st = [[e[k].elapsed_time(e[k + 1]) for k in range(n_ev - 1)] for e in evs]
+                tot = statistics.median(e[0].elapsed_time(e[-1]) for e in evs)
+                merge = [statistics.mean(x[2 + 2 * r] for x in st) for r in range(len(plan))]
+                split = sum(statistics.mean(x[1 + 2 * r] for x in st) for r in range(len(plan)))
+                kb = 8 if kt == mms.KEY_U64 else 4
+                rows.append({"key": name, "n": n, "K": K, "rounds": len(plan), "ms": tot,
+                             "gkeys_per_s": n / tot / 1e6, "tile_sort_ms": statistics.mean(x[0] for x in st),
+                             "merge_pass_ms_avg": statistics.mean(merge) if merge else None,
+                             "merge_pass_hbm_frac": (2 * n * kb / (statistics.mean(merge) / 1e3) / 1e9 / 6787.6)
+                             if merge else None,
+                             "splitters_ms": split, "verified": ok})
+            del src, work, ws
+            torch.cuda.empty_cache()
+    print(json.dumps({"metric": "Gkeys/s by fanout and size", "unit": "Gkeys/s", "n_gpus": 1,
+                      "data": "synthetic", "rows": rows, "all_verified": all(r["verified"] for r in rows)}),
+          flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -611,6 +671,8 @@ def main():
         return run_serve(args)
     if args.workload == "configs":
         return run_configs(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     import numpy as np
     import torch
 
@@ -734,6 +796,29 @@ def main():
         "verified_vs_closed_form": verified,
         "clocks": sampler.summary(t0, t1),
     }
+
+    # The per-pass roofline depends on the fanout: a pass of fanout K runs
+    # ceil(log2 K) on-chip tree levels per HBM read and write.  Measure the
+    # merge pass alone at K = 2 and K = 4 too (same workload, same timing).
+    by_k = {}
+    if not args.pairs:
+        for kf in (2, 4):
+            planf = mms.plan(mms.KEY_U32, N, kf, args.tile)
+            nf = 2 + 2 * len(planf)
+            evf = [[torch.cuda.Event(enable_timing=True) for _ in range(nf)] for _ in range(10)]
+            for i in range(13):
+                work.copy_(src)
+                mms.sort_keys(work, fanout=kf, workspace=ws, kt=mms.KEY_U32, tile_items=args.tile,
+                              events=evf[i - 3] if i >= 3 else None)
+            torch.cuda.synchronize()
+            # merge pass of round r: from event 2 + 2r (after its splitter) to 3 + 2r
+            mf = statistics.mean(statistics.mean(e[2 + 2 * r].elapsed_time(e[3 + 2 * r])
+                                                 for r in range(len(planf)))
+                                 for e in evf)
+            okf = bool(torch.equal(work.to(torch.int64) & 0xFFFFFFFF, torch.arange(N, dtype=torch.int64, device=dev)))
+            by_k[str(kf)] = {"merge_pass_ms": mf, "frac": bytes_pass / (mf / 1e3) / 1e9 / peak,
+                             "sort_ms": statistics.mean(e[0].elapsed_time(e[-1]) for e in evf), "verified": okf}
+        roofline["per_pass_frac_by_fanout"] = by_k
 
     if not args.no_e2e and not args.pairs:
         # End to end: pinned host input -> device -> sort -> host, every step.

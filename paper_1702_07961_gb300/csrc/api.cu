@@ -77,23 +77,75 @@ int tile_warps_for(int key_bytes, const mms_options* opt) {
   return mms::default_tile_warps(key_bytes);
 }
 
-// Fanout of every round.  Auto: the fanout measured fastest on GB300 for the
-// key width (K = 4 for 4-byte keys, K = 8 for 8-byte keys and composites; on
-// this GPU the on-chip merge levels, not HBM traffic, set the pace, so fewer
-// levels per round beat fewer rounds).  Sec. 6.2 tunes K per platform the
-// same way.  The rounds are ceil(log_K(runs)).
+// Fanouts of the merge rounds.  Sec. 6.2 tunes K per platform by
+// measurement; here the planner picks, per sort, the sequence of power-of-two
+// fanouts that minimises a cost model measured on GB300.  A round of fanout K
+// over n items costs about c0 + n * c1[K], where c1 is the merge pass plus
+// splitter time per item at n = 10^8 (bench.py --workload sweep) and c0 the
+// fixed cost of its two launches.  Merge levels cost about the same for
+// K = 4..16, so the optimum first minimises the tree levels ceil(log2 runs)
+// and then the rounds (e.g. (8,8,8,8,4) for 10^8 4-byte keys).  The choice is
+// a coin-change dynamic program over log2 of the coverage.  opt->fanout fixes
+// every round's K instead; the result does not depend on the plan.
+namespace plan_model {
+// ms per 10^8 items of one round (merge pass + splitter), for K = 2, 4, 8, 16, 32
+constexpr double kCost4[5] = {0.238, 0.378, 0.547, 0.746, 1.194};   // 4-byte keys
+constexpr double kCost8[5] = {0.554, 1.020, 1.659, 2.304, 4.169};   // 8-byte keys / composites
+constexpr double kLaunchMs = 0.010;                                 // two launches per round
+}  // namespace plan_model
+
 int plan_rounds(int key_bytes, size_t n, const mms_options* opt, int* K, int maxr) {
   const long long S = 1024ll * tile_warps_for(key_bytes, opt);
   const long long runs = ((long long)n + S - 1) / S;
   if (runs <= 1) return 0;
-  const int fanout = (opt && opt->fanout >= 2) ? opt->fanout : (key_bytes == 8 ? 8 : 4);
-  int rounds = 0;
-  long long cover = 1;
-  while (cover < runs) {
-    cover *= fanout;
-    if (rounds < maxr) K[rounds] = fanout;
-    ++rounds;
+  if (opt && opt->fanout >= 2) {
+    const int fanout = opt->fanout;
+    int rounds = 0;
+    long long cover = 1;
+    while (cover < runs) {
+      cover *= fanout;
+      if (rounds < maxr) K[rounds] = fanout;
+      ++rounds;
+    }
+    return rounds;
   }
+  int L = 0;                                   // levels needed: 2^L >= runs
+  while ((1ll << L) < runs) ++L;
+  const double* c1 = key_bytes == 8 ? plan_model::kCost8 : plan_model::kCost4;
+  const double scale = (double)n / 1e8;
+  // best[l]: least cost of rounds covering at least 2^l; pick[l]: log2 of its first fanout
+  double best[64];
+  int pick[64];
+  best[0] = 0.0;
+  pick[0] = 0;
+  for (int l = 1; l <= L; ++l) {
+    best[l] = 1e300;
+    pick[l] = 1;
+    for (int b = 1; b <= 5; ++b) {
+      const int rest = l - b > 0 ? l - b : 0;
+      const double c = best[rest] + plan_model::kLaunchMs + scale * c1[b - 1];
+      if (c < best[l]) {
+        best[l] = c;
+        pick[l] = b;
+      }
+    }
+  }
+  int rounds = 0;
+  for (int l = L; l > 0;) {
+    const int b = pick[l];
+    if (rounds < maxr) K[rounds] = 1 << b;
+    ++rounds;
+    l = l - b > 0 ? l - b : 0;
+  }
+  // larger fanouts first (the cost model does not depend on the order)
+  const int m = rounds < maxr ? rounds : maxr;
+  for (int a = 0; a < m; ++a)
+    for (int c = a + 1; c < m; ++c)
+      if (K[c] > K[a]) {
+        const int t = K[a];
+        K[a] = K[c];
+        K[c] = t;
+      }
   return rounds;
 }
 
