@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--pairs", action="store_true", help="key + uint32 index payload (stable key-value sort)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-sample", type=int, default=1 << 25)
+    p.add_argument("--cpu-sample", type=int, default=1 << 26)
     p.add_argument("--workload", default="sort", choices=["sort", "batched", "serve", "configs", "sweep"],
                    help="sort: one 10^8-key array per step; batched: 20000 arrays of "
                         "log-uniform size in [2^8, 2^20] with uint32 payloads per step")
