@@ -243,8 +243,8 @@ __global__ void __launch_bounds__(128)
       run_len *= K;
       tpg *= K;
     }
-    splitter_row<KeyT>(in, (long long)d.n, run_len, K, S, idx / tpg, idx % tpg,
-                       table + t * kRowStride);
+    splitter_row<KeyT, 32>(in, (long long)d.n, run_len, K, S, idx / tpg, idx % tpg,
+                           table + t * kRowStride, 0xffffffffu, 0);
   }
 }
 

@@ -1,19 +1,20 @@
 // splitter.cuh -- parallel partitioning of a K-way merge round (Sec. 4.1),
 // shared by the whole-array splitter and the segmented (batched) one.
 //
-// For every output tile j of every group of K sorted runs, one warp finds the
-// pivot indices c[r] (r < K): the number of items run r contributes to the
-// group's first j*S outputs under the strict order (key, run, position).  That
+// For every output tile j of every group of K sorted runs, one lane group
+// (W >= K lanes, 32 / W groups per warp) finds the pivot indices c[r]
+// (r < K): the number of items run r contributes to the group's first j*S
+// outputs under the strict order (key, run, position).  That
 // order makes the pivots unique even with repeated keys (the paper's
 // non-overlap condition, read on the composite key) and equals a stable merge.
 //
 // Search (one lane per run, K <= 32): stride halving on regular samples.  At
-// stride s the warp holds the exact pivots d of the s-sample problem -- the
+// stride s the lane group holds the exact pivots d of the s-sample problem -- the
 // items at positions s-1, 2s-1, ... of every run -- for rank floor(k/s).
 // Halving s adds one candidate per run just above its pivot; the pivots of the
 // s/2-sample problem for rank floor(2k/s) are then the floor(2k/s) smallest of
 // (old selection expanded) + (candidates), found by dropping the largest items
-// from the top with warp arg-max reductions.  At s = 1 the sample problem is
+// from the top with arg-max reductions over the lane group.  At s = 1 the sample problem is
 // the whole problem.  About log2(k) rounds of two independent loads per lane.
 // Positions past a run's end are padding items ordered after every real item
 // (by run, then position).
@@ -47,81 +48,88 @@ __device__ __forceinline__ bool before_cross(const Item<KeyT>& a, int ra, const 
   return ra < rb;
 }
 
-__device__ __forceinline__ uint32_t warp_max_u32(uint32_t v) {
-  return __reduce_max_sync(0xffffffffu, v);
+// Every reduction below runs over one lane group: the lanes of the mask gm
+// (W consecutive lanes aligned to W; all of them execute the call).  A warp
+// holds 32 / W groups, each working on its own output tile.
+__device__ __forceinline__ uint32_t grp_max_u32(unsigned gm, uint32_t v) {
+  return __reduce_max_sync(gm, v);
 }
-__device__ __forceinline__ uint32_t warp_min_u32(uint32_t v) {
-  return __reduce_min_sync(0xffffffffu, v);
+__device__ __forceinline__ uint32_t grp_min_u32(unsigned gm, uint32_t v) {
+  return __reduce_min_sync(gm, v);
 }
 
 // Lanes with `cond` whose key equals the maximum key among them.
-__device__ __forceinline__ unsigned lanes_with_max(bool cond, uint32_t key) {
-  const uint32_t mx = warp_max_u32(cond ? key : 0u);
-  return __ballot_sync(0xffffffffu, cond && key == mx);
+__device__ __forceinline__ unsigned lanes_with_max(unsigned gm, bool cond, uint32_t key) {
+  const uint32_t mx = grp_max_u32(gm, cond ? key : 0u);
+  return __ballot_sync(gm, cond && key == mx);
 }
-__device__ __forceinline__ unsigned lanes_with_max(bool cond, uint64_t key) {
+__device__ __forceinline__ unsigned lanes_with_max(unsigned gm, bool cond, uint64_t key) {
   const uint32_t hi = (uint32_t)(key >> 32), lo = (uint32_t)key;
-  const uint32_t mh = warp_max_u32(cond ? hi : 0u);
+  const uint32_t mh = grp_max_u32(gm, cond ? hi : 0u);
   const bool c2 = cond && hi == mh;
-  const uint32_t ml = warp_max_u32(c2 ? lo : 0u);
-  return __ballot_sync(0xffffffffu, c2 && lo == ml);
+  const uint32_t ml = grp_max_u32(gm, c2 ? lo : 0u);
+  return __ballot_sync(gm, c2 && lo == ml);
 }
-__device__ __forceinline__ unsigned lanes_with_min(bool cond, uint32_t key) {
-  const uint32_t mn = warp_min_u32(cond ? key : 0xffffffffu);
-  return __ballot_sync(0xffffffffu, cond && key == mn);
+__device__ __forceinline__ unsigned lanes_with_min(unsigned gm, bool cond, uint32_t key) {
+  const uint32_t mn = grp_min_u32(gm, cond ? key : 0xffffffffu);
+  return __ballot_sync(gm, cond && key == mn);
 }
-__device__ __forceinline__ unsigned lanes_with_min(bool cond, uint64_t key) {
+__device__ __forceinline__ unsigned lanes_with_min(unsigned gm, bool cond, uint64_t key) {
   const uint32_t hi = (uint32_t)(key >> 32), lo = (uint32_t)key;
-  const uint32_t mh = warp_min_u32(cond ? hi : 0xffffffffu);
+  const uint32_t mh = grp_min_u32(gm, cond ? hi : 0xffffffffu);
   const bool c2 = cond && hi == mh;
-  const uint32_t ml = warp_min_u32(c2 ? lo : 0xffffffffu);
-  return __ballot_sync(0xffffffffu, c2 && lo == ml);
+  const uint32_t ml = grp_min_u32(gm, c2 ? lo : 0xffffffffu);
+  return __ballot_sync(gm, c2 && lo == ml);
 }
 
 // Lane holding the largest item among lanes with `cond` (runs compare by
-// (pad, key, run)); -1 if none.
+// (pad, key, run)); -1 if none.  Lane numbers are the warp's.
 template <typename KeyT>
-__device__ __forceinline__ int warp_argmax(bool cond, const Item<KeyT>& it) {
-  const unsigned any = __ballot_sync(0xffffffffu, cond);
+__device__ __forceinline__ int grp_argmax(unsigned gm, bool cond, const Item<KeyT>& it) {
+  const unsigned any = __ballot_sync(gm, cond);
   if (!any) return -1;
-  const unsigned pads = __ballot_sync(0xffffffffu, cond && it.pad);
+  const unsigned pads = __ballot_sync(gm, cond && it.pad);
   if (pads) return 31 - __clz(pads);
-  return 31 - __clz(lanes_with_max(cond, it.key));
+  return 31 - __clz(lanes_with_max(gm, cond, it.key));
 }
 
 template <typename KeyT>
-__device__ __forceinline__ int warp_argmin(bool cond, const Item<KeyT>& it) {
-  const unsigned any = __ballot_sync(0xffffffffu, cond);
+__device__ __forceinline__ int grp_argmin(unsigned gm, bool cond, const Item<KeyT>& it) {
+  const unsigned any = __ballot_sync(gm, cond);
   if (!any) return -1;
-  const unsigned reals = __ballot_sync(0xffffffffu, cond && !it.pad);
+  const unsigned reals = __ballot_sync(gm, cond && !it.pad);
   if (!reals) return __ffs(any) - 1;
-  return __ffs(lanes_with_min(cond && !it.pad, it.key)) - 1;
+  return __ffs(lanes_with_min(gm, cond && !it.pad, it.key)) - 1;
 }
 
 template <typename KeyT>
-__device__ __forceinline__ Item<KeyT> shfl_item(const Item<KeyT>& it, int src) {
+__device__ __forceinline__ Item<KeyT> shfl_item(unsigned gm, const Item<KeyT>& it, int src) {
   Item<KeyT> o;
-  o.key = __shfl_sync(0xffffffffu, it.key, src);
-  o.pad = __shfl_sync(0xffffffffu, (int)it.pad, src) != 0;
+  o.key = __shfl_sync(gm, it.key, src);
+  o.pad = __shfl_sync(gm, (int)it.pad, src) != 0;
   return o;
 }
 
-__device__ __forceinline__ long long warp_sum_ll(long long v) {
+template <int W>
+__device__ __forceinline__ long long grp_sum_ll(unsigned gm, long long v) {
 #pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = W / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(gm, v, o);
   return v;
 }
 
-// Pivots of output tile j of group g (one warp, one lane per run): row[r]
+// Pivots of output tile j of group g, found by one lane group of W >= K lanes
+// (gm: its lanes, gb: its first lane; lane gb + r handles run r): row[r]
 // receives the number of items of run r among the group's first j * S
-// outputs.  Warp-uniform arguments.
-template <typename KeyT>
+// outputs.  Arguments are uniform over the lane group.
+template <typename KeyT, int W>
 __device__ __forceinline__ void splitter_row(const KeyT* __restrict__ in, long long n,
                                              long long run_len, int K, long long S, long long g,
-                                             long long j, long long* __restrict__ row) {
+                                             long long j, long long* __restrict__ row,
+                                             unsigned gm, int gb) {
   const int lane = threadIdx.x & 31;
-  const bool act = lane < K;
-  const long long rstart = g * run_len * K + (long long)lane * run_len;
+  const int rr = lane - gb;                     // run of this lane
+  const bool act = rr < K;
+  const long long rstart = g * run_len * K + (long long)rr * run_len;
   long long rlen = n - rstart;
   rlen = rlen < 0 ? 0 : (rlen > run_len ? run_len : rlen);
   if (!act) rlen = 0;
@@ -138,32 +146,32 @@ __device__ __forceinline__ void splitter_row(const KeyT* __restrict__ in, long l
     Item<KeyT> o = load_item(run, rlen, ((dd + 1) << sh) - 1);
     Item<KeyT> z{KeyT(0), false};
     if (d >= 1) z = load_item(run, rlen, ((dd - 1) << sh) - 1);
-    const long long jrem = 2 * warp_sum_ll(act ? d : 0) + K - kp;   // items to drop
+    const long long jrem = 2 * grp_sum_ll<W>(gm, act ? d : 0) + K - kp;   // items to drop
     long long cnt = dd + 1;
 
     // Candidates above every selected item are dropped first, in one step.
     const bool hasZ = act && d >= 1;
-    const int mz = warp_argmax(hasZ, e);
+    const int mz = grp_argmax(gm, hasZ, e);
     bool above = act;
     if (mz >= 0) {
-      const Item<KeyT> zmax = shfl_item(e, mz);
+      const Item<KeyT> zmax = shfl_item(gm, e, mz);
       above = act && (lane == mz || before_cross(zmax, mz, o, lane));
     }
-    const unsigned abovem = __ballot_sync(0xffffffffu, above);
+    const unsigned abovem = __ballot_sync(gm, above);
     const long long u = __popc(abovem);
     long long pops;
     if (u <= jrem) {
       if (above) cnt = dd;
       pops = jrem - u;
     } else {                                    // keep only the smallest candidate
-      const int mn = warp_argmin(above, o);
+      const int mn = grp_argmin(gm, above, o);
       if (above && lane != mn) cnt = dd;
       pops = 0;
     }
     // Remaining drops one at a time from the largest current top.
     Item<KeyT> top = (cnt == dd + 1) ? o : e;
     for (long long p = 0; p < pops; ++p) {
-      const int w = warp_argmax(act && cnt >= 1, top);
+      const int w = grp_argmax(gm, act && cnt >= 1, top);
       if (lane == w) {
         cnt -= 1;
         if (cnt >= 1) {
@@ -179,7 +187,7 @@ __device__ __forceinline__ void splitter_row(const KeyT* __restrict__ in, long l
     d = cnt;
     e = top;
   }
-  if (act) row[lane] = d;
+  if (act) row[rr] = d;
 }
 
 }  // namespace mms
