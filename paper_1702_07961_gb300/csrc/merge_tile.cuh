@@ -251,7 +251,7 @@ __device__ __forceinline__ void merge_levels(KeyT* bufX, KeyT* bufY, const int* 
       const int d0 = (item - fi) * kBlockItems;
       const int m = (L - d0) < kBlockItems ? (L - d0) : kBlockItems;
       const int a0 = warp_corank(A, lenA, B, lenB, d0, lane);
-      const int a1 = (d0 + m == L) ? lenA : warp_corank(A, lenA, B, lenB, d0 + m, lane);
+      const int a1 = (d0 + m == L) ? lenA : warp_corank(A, lenA, B, lenB, d0 + m, lane, a0, a0 + m);
       const int X = a1 - a0;
       warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, lane,
                              xout && lv == nl);

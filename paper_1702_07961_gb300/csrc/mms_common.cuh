@@ -169,11 +169,14 @@ __device__ __forceinline__ void lds_if_ge(uint64_t& v, const uint64_t* p, int id
 // ties taken from A (stable).  32-ary: each round all lanes probe positions
 // at an odd stride (distinct banks), a ballot narrows the range 32-fold.
 // ---------------------------------------------------------------------------
+// `lo0` / `hi0` narrow the search when a bracket is known: the co-rank of
+// d + m lies within [co-rank of d, co-rank of d + m] of the block before it.
 template <typename KeyT>
 __device__ __forceinline__ int warp_corank(const KeyT* A, int lenA, const KeyT* B, int lenB,
-                                           int d, int lane) {
-  int lo = d - lenB > 0 ? d - lenB : 0;
+                                           int d, int lane, int lo0 = 0, int hi0 = 0x7fffffff) {
+  int lo = d - lenB > lo0 ? d - lenB : lo0;
   int hi = d < lenA ? d : lenA;
+  hi = hi < hi0 ? hi : hi0;
   while (hi > lo) {
     const int step = ((hi - lo + 31) >> 5) | 1;
     const int i = lo + lane * step;
@@ -389,7 +392,7 @@ __device__ __forceinline__ void cta_merge_level(const KeyT* src, KeyT* dst, int 
       if (item % nwarps != warp) continue;
       const int m = (L - d0) < kBlockItems ? (L - d0) : kBlockItems;
       const int a0 = warp_corank(A, a_len, B, b_len, d0, lane);
-      const int a1 = (d0 + m == L) ? a_len : warp_corank(A, a_len, B, b_len, d0 + m, lane);
+      const int a1 = (d0 + m == L) ? a_len : warp_corank(A, a_len, B, b_len, d0 + m, lane, a0, a0 + m);
       const int X = a1 - a0;
       warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outoff + d0, lane, xout);
     }
