@@ -147,6 +147,26 @@ __device__ __forceinline__ void lds_full_block(KeyT (&v)[32], uint32_t pa, uint3
   (lds_select_imm<32 * Ks, 32 * Ks * (int)sizeof(KeyT)>(v[Ks], pa, pb, lim), ...);
 }
 
+// v = a[0] when idx < lim (signed), b[0] otherwise: one compare, two predicated
+// loads with complementary predicates (each touching consecutive words only).
+__device__ __forceinline__ void lds_pair(uint32_t& v, const uint32_t* a, const uint32_t* b, int idx,
+                                         int lim) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.lt.s32 q, %3, %4;\n\t@q ld.shared.b32 %0, [%1];\n\t"
+      "@!q ld.shared.b32 %0, [%2];\n\t}\n"
+      : "+r"(v)
+      : "r"(smem_u32addr(a)), "r"(smem_u32addr(b)), "r"(idx), "r"(lim)
+      : "memory");
+}
+__device__ __forceinline__ void lds_pair(uint64_t& v, const uint64_t* a, const uint64_t* b, int idx,
+                                         int lim) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.lt.s32 q, %3, %4;\n\t@q ld.shared.b64 %0, [%1];\n\t"
+      "@!q ld.shared.b64 %0, [%2];\n\t}\n"
+      : "+l"(v)
+      : "r"(smem_u32addr(a)), "r"(smem_u32addr(b)), "r"(idx), "r"(lim)
+      : "memory");
+}
 // Loads p[0] into v when idx >= lim (signed).
 __device__ __forceinline__ void lds_if_ge(uint32_t& v, const uint32_t* p, int idx, int lim) {
   asm volatile(
@@ -222,7 +242,7 @@ __device__ __forceinline__ void warp_load_bitonic(const KeyT* A, int X, const Ke
   const int xb = kBlockItems - Y - lane;             // 32k + lane >= 1024 - Y  <=>  32k >= xb
   if (X + Y == kBlockItems) {                        // full block: no pads, xa == xb
 #pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = (32 * k < xa) ? pa[32 * k] : pb[-32 * k];
+    for (int k = 0; k < 32; ++k) lds_pair(v[k], pa + 32 * k, pb - 32 * k, 32 * k, xa);
     return;
   }
 #pragma unroll
