@@ -10,11 +10,15 @@
 //   full   -- the whole block merge;
 //   loads  -- co-ranks and the window loads only;
 //   corank -- the co-rank search only.
-// Each variant runs at reps = 0, 4 and 16.  reps = 0 leaves only the fill
-// (global -> shared, 32 consecutive words per instruction) and the drain
-// (shared -> global, the same), so counts that stay at the reps = 0 level as
-// reps grows do not come from the block merge.  The program checks the merged
-// output of `full` on the host and exits non-zero on a mismatch.
+// On random keys each variant runs at reps = 0, 4 and 16; `full` then runs at
+// reps = 0 and 16 on three more key sets: all keys equal, disjoint lists (every
+// key of the first list below every key of the second), and interleaved lists
+// (even and odd numbers), which move every block window to its extremes.
+// reps = 0 leaves only the fill (global -> shared, 32 consecutive words per
+// instruction) and the drain (shared -> global, the same), so counts that stay
+// at the reps = 0 level as reps grows do not come from the block merge.  The
+// program checks every merged output of `full` on the host and exits non-zero
+// on a mismatch.
 //
 // Build and run (sm_103a):
 //   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -std=c++17 -Iinclude \
@@ -89,37 +93,66 @@ bool run(const char* name, int ctas, const uint32_t* din, uint32_t* dout, int re
   cudaFuncSetAttribute(block_merge_banks<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   block_merge_banks<V><<<ctas, kWarps * 32, smem>>>(din, dout, reps);
   const cudaError_t e = cudaDeviceSynchronize();
-  std::printf("%-6s reps=%-2d %s\n", name, reps, cudaGetErrorString(e));
+  std::printf("%-11s reps=%-2d %s\n", name, reps, cudaGetErrorString(e));
   return e == cudaSuccess;
 }
 
 }  // namespace
 
+// Fills the two sorted lists of every warp: 0 random, 1 all equal, 2 disjoint,
+// 3 interleaved.
+void fill(std::vector<uint32_t>& h, size_t lists, int kind) {
+  std::mt19937 rng(1);
+  for (size_t w = 0; w < lists; ++w) {
+    uint32_t* a = h.data() + w * 2 * kList;
+    uint32_t* b = a + kList;
+    for (int i = 0; i < kList; ++i) {
+      switch (kind) {
+        case 0: a[i] = (uint32_t)rng(); b[i] = (uint32_t)rng(); break;
+        case 1: a[i] = 7u; b[i] = 7u; break;
+        case 2: a[i] = (uint32_t)i; b[i] = (uint32_t)(kList + i); break;
+        default: a[i] = 2u * i; b[i] = 2u * i + 1u; break;
+      }
+    }
+    std::sort(a, a + kList);
+    std::sort(b, b + kList);
+  }
+}
+
+bool check(const std::vector<uint32_t>& h, const uint32_t* dout, size_t lists, const char* name, int reps) {
+  std::vector<uint32_t> got(h.size());
+  cudaMemcpy(got.data(), dout, h.size() * 4, cudaMemcpyDeviceToHost);
+  bool ok = true;
+  for (size_t w = 0; w < lists && ok; ++w) {
+    std::vector<uint32_t> want(h.begin() + w * 2 * kList, h.begin() + (w + 1) * 2 * kList);
+    std::sort(want.begin(), want.end());
+    ok = std::equal(want.begin(), want.end(), got.begin() + w * 2 * kList);
+  }
+  std::printf("full   reps=%-2d %-11s merged output %s\n", reps, name, ok ? "matches" : "MISMATCH");
+  return ok;
+}
+
 int main() {
   const int ctas = 2 * 152;
   const size_t lists = (size_t)ctas * kWarps;
   const size_t n = lists * 2 * kList;
-  std::vector<uint32_t> h(n), got(n);
-  std::mt19937 rng(1);
-  for (auto& x : h) x = (uint32_t)rng();
-  for (size_t w = 0; w < 2 * lists; ++w) std::sort(h.begin() + w * kList, h.begin() + (w + 1) * kList);
+  const char* names[4] = {"random", "equal", "disjoint", "interleaved"};
+  std::vector<uint32_t> h(n);
   uint32_t *din = nullptr, *dout = nullptr;
   if (cudaMalloc(&din, n * 4) != cudaSuccess || cudaMalloc(&dout, n * 4) != cudaSuccess) return 1;
-  cudaMemcpy(din, h.data(), n * 4, cudaMemcpyHostToDevice);
   bool ok = true;
-  for (int reps : {0, 4, 16}) {
-    ok = ok && run<kFull>("full", ctas, din, dout, reps);
-    if (ok && reps > 0) {
-      cudaMemcpy(got.data(), dout, n * 4, cudaMemcpyDeviceToHost);
-      for (size_t w = 0; w < lists && ok; ++w) {
-        std::vector<uint32_t> want(h.begin() + w * 2 * kList, h.begin() + (w + 1) * 2 * kList);
-        std::sort(want.begin(), want.end());
-        ok = std::equal(want.begin(), want.end(), got.begin() + w * 2 * kList);
+  for (int kind = 0; kind < 4 && ok; ++kind) {
+    fill(h, lists, kind);
+    cudaMemcpy(din, h.data(), n * 4, cudaMemcpyHostToDevice);
+    for (int reps : {0, 4, 16}) {
+      if (kind > 0 && reps == 4) continue;
+      ok = ok && run<kFull>(names[kind], ctas, din, dout, reps);
+      if (ok && reps > 0) ok = check(h, dout, lists, names[kind], reps);
+      if (kind == 0) {
+        ok = ok && run<kLoads>("loads", ctas, din, dout, reps);
+        ok = ok && run<kCorank>("corank", ctas, din, dout, reps);
       }
-      std::printf("full   reps=%-2d merged output %s\n", reps, ok ? "matches" : "MISMATCH");
     }
-    ok = ok && run<kLoads>("loads", ctas, din, dout, reps);
-    ok = ok && run<kCorank>("corank", ctas, din, dout, reps);
   }
   cudaFree(din);
   cudaFree(dout);
