@@ -19,7 +19,7 @@ namespace mms {
 
 // Bitonic sorting network over a lane's 32 registers (ascending).
 template <typename KeyT>
-__device__ __forceinline__ void lane_sort32(KeyT (&v)[32]) {
+__device__ __forceinline__ void lane_sort32(KeyT (&v)[32], const MadOnes& c) {
 #pragma unroll
   for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
@@ -29,9 +29,9 @@ __device__ __forceinline__ void lane_sort32(KeyT (&v)[32]) {
         const int ixj = i ^ j;
         if (ixj > i) {
           if ((i & k) == 0)
-            cas(v[i], v[ixj]);
+            cas_mix(v[i], v[ixj], pair_ordinal(i, j), c);
           else
-            cas(v[ixj], v[i]);
+            cas_mix(v[ixj], v[i], pair_ordinal(i, j), c);
         }
       }
     }
@@ -43,36 +43,46 @@ __device__ __forceinline__ void lane_sort32(KeyT (&v)[32]) {
 // 32*l + (j ^ flip_mask(l)), the layout warp_store_block writes out.
 // Level lg merges runs of 2^(lg-1) lanes: a reversed-partner stage across the
 // run pair, lane half-cleaners by shuffle, then in-lane half-cleaners.
+// Every compare-exchange and per-lane min/max pick mixes the ALU and
+// multiply-add forms (cas_mix, pick_mix: half of the picks, whose plain form
+// is a compare and a select, take the multiply-add form).
 template <typename KeyT>
 __device__ __forceinline__ void warp_sort_1024(KeyT (&v)[32], int lane) {
-  lane_sort32(v);
+  constexpr int E = Vec16<KeyT>::E;
+  const MadOnes c = mad_ones();
+  lane_sort32(v, c);
 #pragma unroll
   for (int lg = 1; lg <= 5; ++lg) {
     const int mask = (1 << lg) - 1;
-    const bool upper = (lane & (1 << (lg - 1))) != 0;
+    const uint32_t upper = (lane >> (lg - 1)) & 1;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const KeyT a = v[r], b = v[31 - r];
       const KeyT pa = shfl_xor(b, mask);   // partner's register 31-r pairs with my r
       const KeyT pb = shfl_xor(a, mask);   // partner's register r pairs with my 31-r
-      v[r] = upper ? kmax(a, pa) : kmin(a, pa);
-      v[31 - r] = upper ? kmax(b, pb) : kmin(b, pb);
+      v[r] = pick_mix(a, pa, upper, true, c);
+      v[31 - r] = pick_mix(b, pb, upper, false, c);
     }
 #pragma unroll
     for (int ls = (1 << lg) >> 2; ls >= 1; ls >>= 1) {
-      const bool up = (lane & ls) != 0;
+      const uint32_t up = (lane & ls) ? 1u : 0u;
 #pragma unroll
       for (int r = 0; r < 32; ++r) {
         const KeyT p = shfl_xor(v[r], ls);
-        v[r] = up ? kmax(v[r], p) : kmin(v[r], p);
+        v[r] = pick_mix(v[r], p, up, (r & 1) == 0, c);
       }
     }
 #pragma unroll
     for (int s = 16; s >= 1; s >>= 1) {
-      const bool f = (lg == 5) && ((flip_mask<KeyT>(lane) & s) != 0);
+      const uint32_t f = (flip_mask<KeyT>(lane) & s) ? 1u : 0u;
 #pragma unroll
-      for (int k = 0; k < 32; ++k)
-        if ((k & s) == 0) cas_dir(v[k], v[k + s], f);
+      for (int k = 0; k < 32; ++k) {
+        if ((k & s) != 0) continue;
+        if (lg == 5 && s >= E)
+          cas_dir_mix(v[k], v[k + s], f, pair_ordinal(k, s), c);
+        else
+          cas_mix(v[k], v[k + s], pair_ordinal(k, s), c);
+      }
     }
   }
 }
