@@ -126,13 +126,20 @@ __device__ __forceinline__ void merge_plan_warp(const KeyT* __restrict__ in, lon
     }
     const int R = incl - span;                       // span start of segment `lane`
     const int lpre = lincl - len;                    // items in segments before `lane`
-    // Bulk part: from gsrc - head to the last 16-byte boundary (of absolute
-    // addresses) inside the segment; the rest by plain loads.
+    // Bulk part: from gsrc - head to the first 16-byte boundary (of absolute
+    // addresses) at or past the segment's end.  The span rounds up to that
+    // boundary, so the few items past the segment land in its own span and
+    // are never read.  Where that boundary lies past the end of `in`, the
+    // copy stops at the last boundary inside the segment and plain loads
+    // fetch the rest (at most one tile per pass).
     const long long bulk_lo = gsrc - head;
-    const long long bulk_hi = (in_mis + gsrc + len) / E * E - in_mis;
-    const unsigned bulk_bytes =
-        (act && bulk_hi > bulk_lo) ? (unsigned)((bulk_hi - bulk_lo) * sizeof(KeyT)) : 0u;
-    // Ragged ends, one segment at a time, consecutive lanes -> consecutive words.
+    const long long bulk_up = (in_mis + gsrc + len + E - 1) / E * E - in_mis;
+    const long long bulk_hi = bulk_up <= n ? bulk_up : (in_mis + gsrc + len) / E * E - in_mis;
+    const unsigned bulk_bytes = (act && len > 0 && bulk_hi > bulk_lo)
+                                    ? (unsigned)((bulk_hi - bulk_lo) * sizeof(KeyT))
+                                    : 0u;
+    // Items no bulk copy covers, one segment at a time, consecutive lanes ->
+    // consecutive words.
     auto ragged = [&]() {
       for (int r = 0; r < K; ++r) {
         const long long s_src = __shfl_sync(0xffffffffu, gsrc, r);
@@ -151,7 +158,7 @@ __device__ __forceinline__ void merge_plan_warp(const KeyT* __restrict__ in, lon
     if (lane == 0) mbar_arrive_expect_tx(bar, total);
     __syncwarp();
     if (bulk_bytes) bulk_g2s(stage + R, in + bulk_lo, bulk_bytes, bar);
-    ragged();
+    if (__any_sync(0xffffffffu, act && len > 0 && bulk_hi < gsrc + len)) ragged();
     // Merge-tree nodes, one per lane, in level order: node (level l >= 1,
     // pair q) merges child A = segments [q*2^l, q*2^l + 2^(l-1)) and child
     // B = the rest of [q*2^l, (q+1)*2^l) (clipped to K).
