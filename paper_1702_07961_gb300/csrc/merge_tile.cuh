@@ -64,41 +64,56 @@ inline size_t merge_pass_smem_bytes_impl(int key_bytes, int warps, int K) {
   return 0;
 }
 
-// Plans output tile j of group g and stages its segments into `stage`: one
+// Segment bounds of the tile in run `lane` (lanes < K): from the pivot rows,
+// or the run's ends for a group's first / last tile.  Warp 0 issues these
+// loads first thing, so they are in flight across the CTA's setup.
+__device__ __forceinline__ void merge_tile_pivots(long long n, long long run_len, int K,
+                                                  long long g, long long j,
+                                                  const long long* __restrict__ lo_row,
+                                                  const long long* __restrict__ hi_row, int S,
+                                                  int lane, long long& lo, long long& hi) {
+  const long long gstart = g * run_len * K;
+  const long long grest = n - gstart;
+  const long long gsize = grest < run_len * K ? grest : run_len * K;
+  long long rlen = n - (gstart + (long long)lane * run_len);
+  rlen = rlen < 0 ? 0 : (rlen > run_len ? run_len : rlen);
+  lo = 0;
+  hi = 0;
+  if (lane < K) {
+    lo = (j == 0) ? 0 : lo_row[lane];
+    hi = ((j + 1) * S < gsize) ? hi_row[lane] : rlen;   // not the group's last tile
+  }
+}
+
+// Plans output tile j of group g, whose segment bounds in run `lane` are lo
+// and hi (from merge_tile_pivots), and stages its segments into `stage`: one
 // warp, one lane per run and one per merge-tree node.  Starts the bulk copies
-// on `bar`, loads the ragged ends, and writes the node table and the scalars
-// (levels, nodes, tile size, error) into `ctl`; the caller's CTA barrier
-// publishes the ragged ends and the table, the barrier's phase the copies.
-// On a pivot row that fails its check, ctl's error scalar is set and nothing
-// is staged.
+// on `bar`, loads the items no bulk copy covers, and writes the node table and
+// the scalars (levels, nodes, tile size, error) into `ctl`; the caller's CTA
+// barrier publishes the plain loads and the table, the barrier's phase the
+// copies.  On segment bounds that fail their check, ctl's error scalar is set
+// and nothing is staged.
 template <typename KeyT, int WARPS>
 __device__ __forceinline__ void merge_plan_warp(const KeyT* __restrict__ in, long long n,
                                                 long long run_len, int K, long long g,
-                                                long long j, const long long* __restrict__ lo_row,
-                                                const long long* __restrict__ hi_row, int S,
+                                                long long j, long long lo, long long hi, int S,
                                                 KeyT* stage, int* ctl, uint64_t* bar, int lane) {
   using G = MergeGeom<KeyT, WARPS>;
   constexpr int E = G::E;
   const long long gstart = g * run_len * K;
   const long long grest = n - gstart;
   const long long gsize = grest < run_len * K ? grest : run_len * K;
-  const long long tiles_here = (gsize + S - 1) / S;
   const bool act = lane < K;
   const long long rstart = gstart + (long long)lane * run_len;
   long long rlen = n - rstart;
   rlen = rlen < 0 ? 0 : (rlen > run_len ? run_len : rlen);
-  long long lo = 0, hi = 0;
-  if (act) {
-    lo = (j == 0) ? 0 : lo_row[lane];
-    hi = (j + 1 < tiles_here) ? hi_row[lane] : rlen;
-  }
   // The pivot rows must describe segments inside their runs whose lengths
   // sum to this tile's size; anything else would overrun the staging buffer.
+  // Each segment is checked against S first, so the sum fits 32 bits.
   const long long want = (gsize - j * S) < S ? (gsize - j * S) : S;
-  const bool bad_seg = act && (lo < 0 || hi < lo || hi > rlen);
-  long long sum = act ? hi - lo : 0;
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  const bool bad_seg = act && (lo < 0 || hi < lo || hi > rlen || hi - lo > S);
+  const int len32 = (act && !bad_seg) ? (int)(hi - lo) : 0;
+  const int sum = (int)__reduce_add_sync(0xffffffffu, (unsigned)len32);
   const bool bad = __any_sync(0xffffffffu, bad_seg) || sum != want || K > kMaxFanout || K < 2 ||
                    S > G::S || S < kBlockItems || (smem_u32addr(stage) & 15u) != 0;
   if (lane == 0) {
@@ -113,19 +128,17 @@ __device__ __forceinline__ void merge_plan_warp(const KeyT* __restrict__ in, lon
     const int in_mis = (int)(((uintptr_t)in / sizeof(KeyT)) & (E - 1));
     const int head = act ? (int)((in_mis + gsrc) % E) : 0;   // items copied before the segment
     const int span = (head + len + E - 1) / E * E + G::kSlack;   // staged span + transpose slack
-    int incl = span;
-    int lincl = len;
+    // One scan over (span, len) packed into 16-bit halves: both totals stay
+    // below 2^16 (the spans sum to at most the buffer capacity).
+    static_assert(G::cap(kMaxFanout) < (1 << 16), "packed span scan needs cap < 2^16");
+    int incl = span | (len << 16);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int x = __shfl_up_sync(0xffffffffu, incl, o);
-      const int y = __shfl_up_sync(0xffffffffu, lincl, o);
-      if (lane >= o) {
-        incl += x;
-        lincl += y;
-      }
+      if (lane >= o) incl += x;
     }
-    const int R = incl - span;                       // span start of segment `lane`
-    const int lpre = lincl - len;                    // items in segments before `lane`
+    const int R = (incl & 0xFFFF) - span;            // span start of segment `lane`
+    const int lpre = (incl >> 16) - len;             // items in segments before `lane`
     // Bulk part: from gsrc - head to the first 16-byte boundary (of absolute
     // addresses) at or past the segment's end.  The span rounds up to that
     // boundary, so the few items past the segment land in its own span and
@@ -152,9 +165,7 @@ __device__ __forceinline__ void merge_plan_warp(const KeyT* __restrict__ in, lon
         if (e < s_src + s_len) stage[s_off + (int)(e - s_src)] = in[e];
       }
     };
-    unsigned total = bulk_bytes;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+    const unsigned total = __reduce_add_sync(0xffffffffu, bulk_bytes);
     if (lane == 0) mbar_arrive_expect_tx(bar, total);
     __syncwarp();
     if (bulk_bytes) bulk_g2s(stage + R, in + bulk_lo, bulk_bytes, bar);
@@ -299,10 +310,13 @@ __device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __
   int* ctl = reinterpret_cast<int*>(bar + 2);          // node table and scalars (see above)
   // Every thread is past the previous tile (whose store has read its shared
   // memory) before the staging copies overwrite the buffer.
+  long long lo = 0, hi = 0;
+  if ((threadIdx.x >> 5) == 0)
+    merge_tile_pivots(n, run_len, K, g, j, lo_row, hi_row, S, threadIdx.x & 31, lo, hi);
   __syncthreads();
   if ((threadIdx.x >> 5) == 0)
-    merge_plan_warp<KeyT, WARPS>(in, n, run_len, K, g, j, lo_row, hi_row, S, bufX, ctl, bar,
-                                        threadIdx.x & 31);
+    merge_plan_warp<KeyT, WARPS>(in, n, run_len, K, g, j, lo, hi, S, bufX, ctl, bar,
+                                 threadIdx.x & 31);
   __syncthreads();
   if (ctl[kCtlNodeFields * 32 + 3] || (smem_u32addr(smem_raw) & 1023u) != 0) {
     if (threadIdx.x == 0) set_device_error(dev_err, kDevErrInternal);
