@@ -645,14 +645,22 @@ def run_sweep(args):
                 st = [[e[k].elapsed_time(e[k + 1]) for k in range(n_ev - 1)] for e in evs]
                 tot = statistics.median(e[0].elapsed_time(e[-1]) for e in evs)
                 merge = [statistics.mean(x[2 + 2 * r] for x in st) for r in range(len(plan))]
-                split = sum(statistics.mean(x[1 + 2 * r] for x in st) for r in range(len(plan)))
+                split_r = [statistics.mean(x[1 + 2 * r] for x in st) for r in range(len(plan))]
+                split = sum(split_r)
+                # runs merged per group in each round: K, except in a last round with fewer runs left
+                runs = -(-n // mms.tile_items(kt))
+                merged = []
+                for k in plan:
+                    merged.append(min(k, runs))
+                    runs = -(-runs // k)
                 kb = 8 if kt == mms.KEY_U64 else 4
                 rows.append({"key": name, "n": n, "K": K, "rounds": len(plan), "ms": tot,
                              "gkeys_per_s": n / tot / 1e6, "tile_sort_ms": statistics.mean(x[0] for x in st),
                              "merge_pass_ms_avg": statistics.mean(merge) if merge else None,
                              "merge_pass_hbm_frac": (2 * n * kb / (statistics.mean(merge) / 1e3) / 1e9 / 6787.6)
                              if merge else None,
-                             "splitters_ms": split, "verified": ok})
+                             "splitters_ms": split, "merge_pass_ms": merge, "splitter_ms": split_r,
+                             "runs_merged": merged, "verified": ok})
             del src, work, ws
             torch.cuda.empty_cache()
     print(json.dumps({"metric": "Gkeys/s by fanout and size", "unit": "Gkeys/s", "n_gpus": 1,

@@ -128,3 +128,27 @@ def load_table(path: str):
     with open(path) as f:
         r = json.load(f)
     return {int(c): int(k) for c, k in r["class_fanout"].items()}, int(r["tile_items"])
+
+
+def fit_plan_costs(rows, n: int = 10**8) -> dict:
+    """Per-round costs of the whole-array planner, from `bench.py --workload
+    sweep` rows: for each key width and K in CANDIDATE_K, the mean time of a
+    round (splitter + merge pass) over the rounds that merged K runs per group,
+    in ms per 10^8 items.  A plan's last round often merges fewer runs than its
+    K (fewer tree levels, so cheaper) and is left out, so that the cost of a
+    full round is not underestimated.  Returns {"u32": [...], "u64": [...]}
+    in the order of CANDIDATE_K (the planner's kCost4 / kCost8)."""
+    out = {}
+    for key in ("u32", "u64"):
+        costs = []
+        for K in CANDIDATE_K:
+            vals = []
+            for r in rows:
+                if r["key"] != key or r["n"] != n or r["K"] != K:
+                    continue
+                for m, s, runs in zip(r["merge_pass_ms"], r["splitter_ms"], r["runs_merged"]):
+                    if runs == K:
+                        vals.append((m + s) * 1e8 / n)
+            costs.append(statistics.mean(vals) if vals else None)
+        out[key] = costs
+    return out

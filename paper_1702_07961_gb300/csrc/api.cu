@@ -81,16 +81,19 @@ int tile_warps_for(int key_bytes, const mms_options* opt) {
 // measurement; here the planner picks, per sort, the sequence of power-of-two
 // fanouts that minimises a cost model measured on GB300.  A round of fanout K
 // over n items costs about c0 + n * c1[K], where c1 is the merge pass plus
-// splitter time per item at n = 10^8 (bench.py --workload sweep) and c0 the
-// fixed cost of its two launches.  Merge levels cost about the same for
+// splitter time per item at n = 10^8 over the rounds that merged K runs per
+// group (bench.py --workload sweep, fitted by autotune.fit_plan_costs) and c0
+// the fixed cost of its two launches.  A last round over fewer runs builds
+// its tree over those runs only, so it costs what a round of the next power
+// of two does.  Merge levels cost about the same for
 // K = 4..16, so the optimum first minimises the tree levels ceil(log2 runs)
 // and then the rounds (e.g. (8,8,8,8,4) for 10^8 4-byte keys).  The choice is
 // a coin-change dynamic program over log2 of the coverage.  opt->fanout fixes
 // every round's K instead; the result does not depend on the plan.
 namespace plan_model {
 // ms per 10^8 items of one round (merge pass + splitter), for K = 2, 4, 8, 16, 32
-constexpr double kCost4[5] = {0.238, 0.378, 0.547, 0.746, 1.194};   // 4-byte keys
-constexpr double kCost8[5] = {0.554, 1.020, 1.659, 2.304, 4.169};   // 8-byte keys / composites
+constexpr double kCost4[5] = {0.230, 0.356, 0.518, 0.723, 1.134};   // 4-byte keys
+constexpr double kCost8[5] = {0.519, 1.001, 1.514, 2.262, 3.940};   // 8-byte keys / composites
 constexpr double kLaunchMs = 0.010;                                 // two launches per round
 }  // namespace plan_model
 

@@ -7,10 +7,12 @@
 // every run (Sec. 4.1), so the tile's inputs are K contiguous segments whose
 // lengths sum to S.  The CTA:
 //   1. stages the K segments into shared memory with 1-D TMA bulk copies
-//      (cp.async.bulk, one mbarrier; the < 16-byte ragged ends of each
-//      segment by plain loads), so every input byte is read from HBM once;
-//   2. merges them along a binary merge tree of ceil(log2 K) levels (the
-//      paper's minBlockHeap has the same levels), one level at a time: every
+//      (cp.async.bulk between 16-byte boundaries, one mbarrier; plain loads
+//      only where a boundary would lie past the end of the array), so every
+//      input byte is read from HBM once;
+//   2. merges them along a binary merge tree of ceil(log2 K') levels, K' <= K
+//      the runs the group holds (the paper's minBlockHeap has the same
+//      levels), one level at a time: every
 //      tree node of the level (a pair of sequences) is cut into 1024-item
 //      output blocks, the blocks of the level are dealt to the warps, and a
 //      CTA barrier separates the levels.  A node's output is written into the
@@ -172,10 +174,16 @@ __device__ __forceinline__ void merge_plan_warp(const KeyT* __restrict__ in, lon
     if (__any_sync(0xffffffffu, act && len > 0 && bulk_hi < gsrc + len)) ragged();
     // Merge-tree nodes, one per lane, in level order: node (level l >= 1,
     // pair q) merges child A = segments [q*2^l, q*2^l + 2^(l-1)) and child
-    // B = the rest of [q*2^l, (q+1)*2^l) (clipped to K).
+    // B = the rest of [q*2^l, (q+1)*2^l) (segments past the group's runs are
+    // empty).
+    // The tree spans the group's runs that exist: the last group of a round
+    // (or a round's only group) may hold fewer than K, and empty leaves would
+    // add levels that only copy.  At least two leaves, so that the tile is
+    // always merged into span start 0.
+    const int kruns = __popc(__ballot_sync(0xffffffffu, act && rlen > 0));
     int nl = 0, nnodes = 0, c_level = 0, c_pair = 0;
     {
-      int cnt = K, idx = 0;
+      int cnt = kruns > 2 ? kruns : 2, idx = 0;
       for (int l = 1; cnt > 1; ++l) {
         const int pairs = (cnt + 1) >> 1;
         if (lane >= idx && lane < idx + pairs) {

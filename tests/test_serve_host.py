@@ -69,3 +69,19 @@ def test_poisson_arrivals_rate():
     assert abs(t[-1] / 20000 - 1 / 250.0) < 0.05 / 250.0 * 10
     gaps = np.diff(t)
     assert abs(np.std(gaps) / np.mean(gaps) - 1.0) < 0.05      # exponential gaps: CV = 1
+
+
+def test_plan_cost_fit_skips_partial_last_rounds():
+    """fit_plan_costs averages only rounds that merged K runs per group."""
+    from paper_1702_07961_gb300.autotune import fit_plan_costs
+    rows = []
+    for key in ("u32", "u64"):
+        for K in (2, 4, 8, 16, 32):
+            # two full rounds at 1.0 + 0.1 ms, then a last round over 3 runs at 0.5 + 0.1 ms
+            rows.append({"key": key, "n": 10**8, "K": K, "merge_pass_ms": [1.0, 1.0, 0.5],
+                         "splitter_ms": [0.1, 0.1, 0.1], "runs_merged": [K, K, min(K, 3)]})
+    got = fit_plan_costs(rows)
+    # K = 2: every round merged 2 runs, the last included (0.6 ms); K >= 4: the last is left out
+    assert got["u32"][0] == pytest.approx((1.1 + 1.1 + 0.6) / 3)
+    for c in got["u32"][1:] + got["u64"][1:]:
+        assert c == pytest.approx(1.1)
