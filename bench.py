@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--arrays", type=int, default=20000)
     p.add_argument("--retune", action="store_true", help="batched: re-run the autotuner")
     p.add_argument("--requests", type=int, default=100, help="serve: requests per arrival-rate run")
+    p.add_argument("--slots", type=int, default=4, help="serve: launch slots (streams) of the server")
+    p.add_argument("--small-max", type=int, default=1 << 20,
+                   help="serve: requests of at most this many keys are coalesced (0: no coalescing)")
     p.add_argument("--max-swaps", type=float, default=1e8,
                    help="configs: largest sortedness swap count r (10^9 takes minutes on the host)")
     return p.parse_args()
@@ -427,7 +430,7 @@ def run_serve(args):
     alone = [(bits(r.out_keys).copy(), None if r.out_values is None else bits(r.out_values).copy())
              for r in reqs]
 
-    srv = serve.SortServer(budget_bytes=40 << 30, slots=4)
+    srv = serve.SortServer(budget_bytes=40 << 30, slots=args.slots, small_max=args.small_max)
     reset(np.zeros(count))
     srv.run(reqs)                                     # warm-up of the server's kernels and arena
     torch.cuda.synchronize()
@@ -472,7 +475,10 @@ def run_serve(args):
         "config": {"workload": f"{count} requests, sizes log-uniform in [2^10, 2^26] ({total_keys} keys), key type "
                                "uniform over {u32, u64, f32}, half with uint32 values, keys from host memory and "
                                "results back to host; Poisson arrivals at 0.5, 1, 2 and 4 times the serial "
-                               "capacity; 40 GB device budget, 4 launch slots, requests <= 2^20 keys coalesced",
+                               f"capacity; 40 GB device budget, {args.slots} launch slots, "
+                               + (f"requests <= {args.small_max} keys coalesced" if args.small_max > 0
+                                  else "no coalescing"),
+                   "slots": args.slots, "small_max": args.small_max,
                    "global_batch": total_keys, "seq_len": None, "parallelism": "single GPU",
                    "serial_capacity_req_per_s": capacity},
         "sweep": sweep,

@@ -385,3 +385,19 @@ def test_sort_merge_tile_sizes(gpu, fanout, merge_tile):
     t = to_dev(keys)
     gpu.sort_keys(t, fanout=fanout, kt=gpu.KEY_U32, merge_tile_items=merge_tile)
     assert_bits_equal(to_host(t, np.uint32), want)
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64, np.float32])
+@pytest.mark.parametrize("tiles,tail,fanout", [(3, 7, 8), (5, 100, 4), (9, 0, 8), (17, 1, 16),
+                                               (33, 4095, 32), (6, 0, 4)])
+def test_sort_groups_with_fewer_runs_than_k(gpu, dtype, tiles, tail, fanout):
+    """Last groups holding fewer runs than K (down to one run, ragged or not):
+    the merge tree spans the runs the group holds, with the same bits."""
+    T = gpu.tile_items(gpu.KEY_U64 if dtype == np.uint64 else gpu.KEY_U32)
+    n = tiles * T + tail
+    if dtype == np.float32:
+        keys = synth.normal_f32(n, 11 * tiles + fanout)
+    else:
+        keys = synth.uniform(n, 13 * tiles + fanout, dtype)
+    want, _ = oracle.sort(keys)
+    assert_bits_equal(gpu_sort(gpu, keys, fanout), want)
