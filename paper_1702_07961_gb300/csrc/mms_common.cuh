@@ -317,6 +317,69 @@ __device__ __forceinline__ int flip_mask(int lane) {
   return (lane & (32 / E - 1)) * E;
 }
 
+// Pieces of the warp's bitonic networks over 1024 items, 32 per lane.  In the
+// striped layout register k of lane l holds item 32k + l (row k, column l); in
+// the blocked layout lane l holds row l, item 32l + j in register j.
+
+// Half-cleaners of register distance D, D/2, .., 1 (strides 32D .. 32 of the
+// striped layout), ascending.
+template <int D, typename KeyT>
+__device__ __forceinline__ void striped_stages(KeyT (&v)[32], const MadOnes& c) {
+#pragma unroll
+  for (int s = D; s >= 1; s >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      if ((k & s) == 0) cas_mix(v[k], v[k + s], pair_ordinal(k, s), c);
+  }
+}
+
+// Striped -> blocked through `out` (16-byte aligned, 32 * nr items): row k is
+// stored with its 16-byte chunks XOR-swizzled by k & 7 (item 32k + l at word
+// 32k + (l ^ E*(k & 7))), so the scalar row stores and the 16-byte row loads
+// are both conflict-free.  Rows at or above nr are not stored; lanes at or
+// above nr receive pads.
+template <typename KeyT>
+__device__ __forceinline__ void striped_to_blocked(KeyT (&v)[32], KeyT* out, int nr, int lane) {
+  using V = Vec16<KeyT>;
+  constexpr int E = V::E;
+#pragma unroll
+  for (int k = 0; k < 32; ++k)
+    if (k < nr) out[32 * k + (lane ^ (E * (k & 7)))] = v[k];
+  __syncwarp();
+  if (lane < nr) {
+    const typename V::T* row = reinterpret_cast<const typename V::T*>(out + 32 * lane);
+    const int sw = lane & 7;
+#pragma unroll
+    for (int ch = 0; ch < 32 / E; ++ch) V::unpack(row[ch ^ sw], &v[ch * E]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = key_pad<KeyT>();
+  }
+  __syncwarp();
+}
+
+// Half-cleaners of stride 16 .. 1 inside the lane (blocked layout).  FLIP:
+// the strides of 16 bytes and more run in the direction of the lane's
+// flip_mask bit, leaving register j with item 32l + (j ^ flip_mask(l)) -- the
+// layout warp_store_block writes out; otherwise all ascending.
+template <bool FLIP, typename KeyT>
+__device__ __forceinline__ void blocked_stages(KeyT (&v)[32], int lane, const MadOnes& c) {
+  constexpr int E = Vec16<KeyT>::E;
+  const int F = flip_mask<KeyT>(lane);
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const uint32_t f = (F & s) ? 1u : 0u;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      if ((k & s) != 0) continue;
+      if (FLIP && s >= E)
+        cas_dir_mix(v[k], v[k + s], f, pair_ordinal(k, s), c);
+      else
+        cas_mix(v[k], v[k + s], pair_ordinal(k, s), c);   // F has no bit below E
+    }
+  }
+}
+
 // Runs the bitonic merge of the 1024 items in v (striped layout).  The
 // striped -> blocked transpose goes through the block's own output region
 // `out` (16-byte aligned, at least 32 * nr items): row k (items 32k .. 32k+31)
@@ -328,47 +391,11 @@ __device__ __forceinline__ int flip_mask(int lane) {
 // pads) and are neither stored nor loaded.
 template <typename KeyT>
 __device__ __forceinline__ void warp_bitonic_1024(KeyT (&v)[32], KeyT* out, int nr, int lane) {
-  using V = Vec16<KeyT>;
-  constexpr int E = V::E;
   const MadOnes c = mad_ones();
-  // half-cleaners of stride 512 .. 32: register distance 16 .. 1
-#pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-#pragma unroll
-    for (int k = 0; k < 32; ++k)
-      if ((k & s) == 0) cas_mix(v[k], v[k + s], pair_ordinal(k, s), c);
-  }
-  // striped -> blocked: item 32k + lane at word 32k + (lane ^ E*(k & 7))
-#pragma unroll
-  for (int k = 0; k < 32; ++k)
-    if (k < nr) out[32 * k + (lane ^ (E * (k & 7)))] = v[k];
-  __syncwarp();
-  if (lane < nr) {
-    const typename V::T* row = reinterpret_cast<const typename V::T*>(out + 32 * lane);
-    const int sw = lane & 7;
-#pragma unroll
-    for (int c = 0; c < 32 / E; ++c) V::unpack(row[c ^ sw], &v[c * E]);
-  } else {
-#pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = key_pad<KeyT>();
-  }
-  __syncwarp();
-  // half-cleaners of stride 16 .. 1 inside the lane
-  const int F = flip_mask<KeyT>(lane);
-#pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-    const uint32_t f = (F & s) ? 1u : 0u;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      if ((k & s) != 0) continue;
-      if (s >= E)
-        cas_dir_mix(v[k], v[k + s], f, pair_ordinal(k, s), c);
-      else
-        cas_mix(v[k], v[k + s], pair_ordinal(k, s), c);   // F has no bit below E
-    }
-  }
+  striped_stages<16>(v, c);                          // strides 512 .. 32
+  striped_to_blocked(v, out, nr, lane);
+  blocked_stages<true>(v, lane, c);                  // strides 16 .. 1, store layout
 }
-
 __device__ __forceinline__ void sts_addr(uint32_t addr, uint32_t v) {
   asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }

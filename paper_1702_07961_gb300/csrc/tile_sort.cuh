@@ -38,53 +38,65 @@ __device__ __forceinline__ void lane_sort32(KeyT (&v)[32], const MadOnes& c) {
   }
 }
 
-// Sorts 1024 keys held as 32 per lane (any assignment) into the blocked
-// layout: after the call register j of lane l holds sorted item
-// 32*l + (j ^ flip_mask(l)), the layout warp_store_block writes out.
-// Level lg merges runs of 2^(lg-1) lanes: a reversed-partner stage across the
-// run pair, lane half-cleaners by shuffle, then in-lane half-cleaners.
-// Every compare-exchange and per-lane min/max pick mixes the ALU and
-// multiply-add forms (cas_mix, pick_mix: half of the picks, whose plain form
-// is a compare and a select, take the multiply-add form).
-template <typename KeyT>
-__device__ __forceinline__ void warp_sort_1024(KeyT (&v)[32], int lane) {
+// Blocked -> striped through `scratch` (16-byte aligned, 1024 items), with the
+// second half of every block of R rows read backwards.  On return register k
+// of lane l holds item 32k + l of the sequence in which every block of R rows
+// is its first R/2 rows in order followed by its last R/2 rows in reverse
+// (row qR + R - 1 - i into register qR + R/2 + i, column 31 - l into lane l):
+// a bitonic sequence when both halves of the block are ascending, so an
+// ascending half-cleaner cascade sorts it, with no per-lane directions.  Each
+// lane writes its row as 16-byte chunks XOR-swizzled by row & 7, and each
+// register load reads 32 distinct words of one row: no bank conflicts.
+template <int R, typename KeyT>
+__device__ __forceinline__ void blocked_to_striped_rev(KeyT (&v)[32], KeyT* scratch, int lane) {
   constexpr int E = Vec16<KeyT>::E;
+  const uint32_t row = smem_u32addr(scratch + 32 * lane);
+  const int sw = lane & 7;
+#pragma unroll
+  for (int ch = 0; ch < 32 / E; ++ch)
+    sts128(row + (uint32_t)((ch ^ sw) * E * (int)sizeof(KeyT)), &v[ch * E]);
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const int kq = k % R;
+    const bool rev = kq >= R / 2;
+    const int src = rev ? k - kq + R - 1 - (kq - R / 2) : k;   // source row
+    const int w = rev ? 31 - lane : lane;                      // source column
+    v[k] = scratch[32 * src + (w ^ (E * (src & 7)))];
+  }
+  __syncwarp();
+}
+
+// One level of the warp sort: every block of R rows, whose two halves are
+// each sorted, becomes sorted (blocked layout in and out).
+template <int R, typename KeyT>
+__device__ __forceinline__ void warp_merge_rows(KeyT (&v)[32], KeyT* scratch, int lane,
+                                                const MadOnes& c) {
+  blocked_to_striped_rev<R>(v, scratch, lane);
+  striped_stages<R / 2>(v, c);                       // strides 16R .. 32
+  striped_to_blocked(v, scratch, 32, lane);
+  blocked_stages<false>(v, lane, c);                 // strides 16 .. 1
+}
+
+// Sorts 1024 keys held as 32 per lane (any assignment): each lane sorts its
+// 32 keys (a row), then levels of 64, 128, 256, 512 and 1024 keys merge pairs
+// of sorted blocks with bitonic cascades -- strides of 32 and more between
+// registers in the striped layout, the rest inside the lane -- through
+// conflict-free transposes in the warp's 1024-item `scratch` (no shuffles).
+// After the call register j of lane l holds sorted item 32*l + (j ^
+// flip_mask(l)), the layout warp_store_block writes out.
+template <typename KeyT>
+__device__ __forceinline__ void warp_sort_1024(KeyT (&v)[32], KeyT* scratch, int lane) {
   const MadOnes c = mad_ones();
   lane_sort32(v, c);
-#pragma unroll
-  for (int lg = 1; lg <= 5; ++lg) {
-    const int mask = (1 << lg) - 1;
-    const uint32_t upper = (lane >> (lg - 1)) & 1;
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const KeyT a = v[r], b = v[31 - r];
-      const KeyT pa = shfl_xor(b, mask);   // partner's register 31-r pairs with my r
-      const KeyT pb = shfl_xor(a, mask);   // partner's register r pairs with my 31-r
-      v[r] = pick_mix(a, pa, upper, true, c);
-      v[31 - r] = pick_mix(b, pb, upper, false, c);
-    }
-#pragma unroll
-    for (int ls = (1 << lg) >> 2; ls >= 1; ls >>= 1) {
-      const uint32_t up = (lane & ls) ? 1u : 0u;
-#pragma unroll
-      for (int r = 0; r < 32; ++r) {
-        const KeyT p = shfl_xor(v[r], ls);
-        v[r] = pick_mix(v[r], p, up, (r & 1) == 0, c);
-      }
-    }
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-      const uint32_t f = (flip_mask<KeyT>(lane) & s) ? 1u : 0u;
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        if ((k & s) != 0) continue;
-        if (lg == 5 && s >= E)
-          cas_dir_mix(v[k], v[k + s], f, pair_ordinal(k, s), c);
-        else
-          cas_mix(v[k], v[k + s], pair_ordinal(k, s), c);
-      }
-    }
-  }
+  warp_merge_rows<2>(v, scratch, lane, c);
+  warp_merge_rows<4>(v, scratch, lane, c);
+  warp_merge_rows<8>(v, scratch, lane, c);
+  warp_merge_rows<16>(v, scratch, lane, c);
+  blocked_to_striped_rev<32>(v, scratch, lane);      // the last level: the block merge's network
+  striped_stages<16>(v, c);
+  striped_to_blocked(v, scratch, 32, lane);
+  blocked_stages<true>(v, lane, c);
 }
 
 template <typename KeyT, bool XIN>
@@ -123,9 +135,10 @@ __device__ __forceinline__ void tile_sort_finish(KeyT (&v)[32], KeyT* out, long 
   KeyT* bufY = bufX + T + kTileSlack;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  warp_sort_1024(v, lane);
-  // The previous tile of a persistent CTA has been read out of shared memory.
+  // The previous tile of a persistent CTA has been read out of shared memory
+  // before the warps use it as transpose scratch.
   __syncthreads();
+  warp_sort_1024(v, bufX + warp * kBlockItems, lane);
   const long long trem = n - base;
   const int m = trem >= T ? T : (int)trem;
   if constexpr (WARPS == 1) {
