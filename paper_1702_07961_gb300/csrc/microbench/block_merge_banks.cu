@@ -9,7 +9,8 @@
 // runs.  Variants:
 //   full   -- the whole block merge;
 //   loads  -- co-ranks and the window loads only;
-//   corank -- the co-rank search only.
+//   corank -- the co-rank search only;
+//   wsort  -- the tile sort's warp sort of 1024 keys (random keys only).
 // On random keys each variant runs at reps = 0, 4 and 16; `full` then runs at
 // reps = 0 and 16 on three more key sets: all keys equal, disjoint lists (every
 // key of the first list below every key of the second), and interleaved lists
@@ -33,6 +34,7 @@
 #include <vector>
 
 #include "../mms_common.cuh"
+#include "../tile_sort.cuh"
 
 using namespace mms;
 
@@ -41,7 +43,7 @@ namespace {
 constexpr int kList = 1024;                 // keys per input list
 constexpr int kWarps = 5;                   // warps per CTA
 constexpr int kWarpWords = 4 * kList + 64;  // A, B, 2048-key output, slack (16-byte multiple)
-enum Variant { kFull = 0, kLoads = 1, kCorank = 2 };
+enum Variant { kFull = 0, kLoads = 1, kCorank = 2, kWarpSort = 3 };
 
 template <int V>
 __global__ void __launch_bounds__(kWarps * 32) block_merge_banks(const uint32_t* in, uint32_t* out_g,
@@ -60,6 +62,17 @@ __global__ void __launch_bounds__(kWarps * 32) block_merge_banks(const uint32_t*
   for (int i = lane; i < 2 * kList; i += 32) out[i] = 0;
   __syncwarp();
   uint32_t acc = 0;
+  if constexpr (V == kWarpSort) {
+    // The tile sort's warp sort of 1024 keys (x = A xor B, item 32j + lane in
+    // register j), `reps` times, with its transposes in `out`; then stored.
+    uint32_t v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = A[32 * j + lane] ^ B[32 * j + lane];
+    for (int rep = 0; rep < reps; ++rep) warp_sort_1024(v, out, lane);
+    if (reps > 0) warp_store_block<uint32_t>(out, kBlockItems, v, lane, false);
+    __syncwarp();
+    reps = 0;
+  }
   for (int rep = 0; rep < reps; ++rep) {
     for (int d0 = 0; d0 < 2 * kList; d0 += kBlockItems) {
       if constexpr (V == kCorank) {
@@ -132,6 +145,23 @@ bool check(const std::vector<uint32_t>& h, const uint32_t* dout, size_t lists, c
   return ok;
 }
 
+// The warp-sort variant's output: each warp's x = A xor B, sorted, then zeros.
+bool check_wsort(const std::vector<uint32_t>& h, const uint32_t* dout, size_t lists, int reps) {
+  std::vector<uint32_t> got(h.size());
+  cudaMemcpy(got.data(), dout, h.size() * 4, cudaMemcpyDeviceToHost);
+  bool ok = true;
+  for (size_t w = 0; w < lists && ok; ++w) {
+    const uint32_t* a = h.data() + w * 2 * kList;
+    std::vector<uint32_t> want(kList);
+    for (int i = 0; i < kList; ++i) want[i] = a[i] ^ a[kList + i];
+    std::sort(want.begin(), want.end());
+    ok = std::equal(want.begin(), want.end(), got.begin() + w * 2 * kList);
+    for (int i = kList; i < 2 * kList && ok; ++i) ok = got[w * 2 * kList + i] == 0u;
+  }
+  std::printf("wsort  reps=%-2d random      sorted output %s\n", reps, ok ? "matches" : "MISMATCH");
+  return ok;
+}
+
 int main() {
   const int ctas = 2 * 152;
   const size_t lists = (size_t)ctas * kWarps;
@@ -151,6 +181,8 @@ int main() {
       if (kind == 0) {
         ok = ok && run<kLoads>("loads", ctas, din, dout, reps);
         ok = ok && run<kCorank>("corank", ctas, din, dout, reps);
+        ok = ok && run<kWarpSort>("wsort", ctas, din, dout, reps);
+        if (ok && reps > 0) ok = check_wsort(h, dout, lists, reps);
       }
     }
   }
