@@ -155,7 +155,7 @@ __device__ __forceinline__ void merge_plan_warp(const KeyT* __restrict__ in, lon
                                     : 0u;
     // Items no bulk copy covers, one segment at a time, consecutive lanes ->
     // consecutive words.
-    auto ragged = [&]() {
+    auto plain_tail = [&]() {
       for (int r = 0; r < K; ++r) {
         const long long s_src = __shfl_sync(0xffffffffu, gsrc, r);
         const int s_len = __shfl_sync(0xffffffffu, len, r);
@@ -171,7 +171,7 @@ __device__ __forceinline__ void merge_plan_warp(const KeyT* __restrict__ in, lon
     if (lane == 0) mbar_arrive_expect_tx(bar, total);
     __syncwarp();
     if (bulk_bytes) bulk_g2s(stage + R, in + bulk_lo, bulk_bytes, bar);
-    if (__any_sync(0xffffffffu, act && len > 0 && bulk_hi < gsrc + len)) ragged();
+    if (__any_sync(0xffffffffu, act && len > 0 && bulk_hi < gsrc + len)) plain_tail();
     // Merge-tree nodes, one per lane, in level order: node (level l >= 1,
     // pair q) merges child A = segments [q*2^l, q*2^l + 2^(l-1)) and child
     // B = the rest of [q*2^l, (q+1)*2^l) (segments past the group's runs are
@@ -332,7 +332,7 @@ __device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __
   }
   // One thread polls the staging barrier; the others wait at the CTA barrier
   // (no issue slots spent polling), which also orders the staged data and the
-  // ragged-end stores before every warp's reads.
+  // plainly loaded items before every warp's reads.
   const bool ok = (threadIdx.x == 0) ? mbar_wait_bounded(bar, phase) : true;
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) set_device_error(dev_err, kDevErrTimeout);

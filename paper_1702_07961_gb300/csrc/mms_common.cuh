@@ -159,25 +159,6 @@ __device__ __forceinline__ void cas_dir_mix(uint64_t& a, uint64_t& b, uint32_t f
   cas_dir(a, b, f != 0);
 }
 
-// up ? max(v, p) : min(v, p), with up in {0, 1}; `mad` picks the form.
-__device__ __forceinline__ uint32_t pick_mix(uint32_t v, uint32_t p, uint32_t up, bool mad,
-                                             const MadOnes& c) {
-  if (mad) {
-    const uint32_t lo = min(v, p);
-    const uint32_t d = mad_u32(lo, c.m2, mad_u32(v, c.one, p));   // max - min
-    return mad_u32(up, d, lo);
-  }
-  return up ? max(v, p) : min(v, p);
-}
-__device__ __forceinline__ uint64_t pick_mix(uint64_t v, uint64_t p, uint32_t up, bool,
-                                             const MadOnes&) {
-  return up ? kmax(v, p) : kmin(v, p);
-}
-
-template <typename KeyT>
-__device__ __forceinline__ KeyT shfl_xor(KeyT v, int mask) {
-  return __shfl_xor_sync(0xffffffffu, v, mask);
-}
 
 // ---------------------------------------------------------------------------
 // Shared-memory accesses the compiler may not merge or reorder across.

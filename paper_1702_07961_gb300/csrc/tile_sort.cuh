@@ -6,9 +6,10 @@
 // The paper's base case is a per-warp shearsort of a 32 x 32 grid, extended
 // by bitonic merges between warps.  Here each lane sorts the 32 keys it loaded
 // with an in-register sorting network, the warp finishes its 1024 keys with
-// register/shuffle bitonic merges (no shared memory, so no bank traffic), and
-// the CTA merges the warps' blocks with the same conflict-free block merge the
-// merge rounds use.  HBM traffic: one coalesced 128-bit read and one coalesced
+// bitonic merges through conflict-free transposes in its share of the tile
+// buffer (the row/column transposes of shearsort, swizzled), and the CTA
+// merges the warps' blocks with the same conflict-free block merge the merge
+// rounds use.  HBM traffic: one coalesced 128-bit read and one coalesced
 // 128-bit write of every key.
 #pragma once
 
