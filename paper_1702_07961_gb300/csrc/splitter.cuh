@@ -110,13 +110,6 @@ __device__ __forceinline__ Item<KeyT> shfl_item(unsigned gm, const Item<KeyT>& i
   return o;
 }
 
-template <int W>
-__device__ __forceinline__ long long grp_sum_ll(unsigned gm, long long v) {
-#pragma unroll
-  for (int o = W / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(gm, v, o);
-  return v;
-}
-
 // Pivots of output tile j of group g, found by one lane group of W >= K lanes
 // (gm: its lanes, gb: its first lane; lane gb + r handles run r): row[r]
 // receives the number of items of run r among the group's first j * S
@@ -146,7 +139,10 @@ __device__ __forceinline__ void splitter_row(const KeyT* __restrict__ in, long l
     Item<KeyT> o = load_item(run, rlen, ((dd + 1) << sh) - 1);
     Item<KeyT> z{KeyT(0), false};
     if (d >= 1) z = load_item(run, rlen, ((dd - 1) << sh) - 1);
-    const long long jrem = 2 * grp_sum_ll<W>(gm, act ? d : 0) + K - kp;   // items to drop
+    // Items to drop: (sum of the lanes' 2d + 1) - kp, which lies in [0, K];
+    // one 32-bit warp reduction, exact modulo 2^32 since the result is small.
+    const unsigned dsum = __reduce_add_sync(gm, act ? (unsigned)d : 0u);
+    const long long jrem = (int)(2u * dsum + (unsigned)K - (unsigned)kp);
     long long cnt = dd + 1;
 
     // Candidates above every selected item are dropped first, in one step.
