@@ -863,7 +863,7 @@ def main():
         for i in range(2 * ns):                             # warm-up of every slot
             e2e_step(slots[i % ns])
         torch.cuda.synchronize()
-        n_e2e = max(6, args.steps // 5)
+        n_e2e = max(12, args.steps // 2)
         start = torch.cuda.Event(enable_timing=True)
         start.record(slots[0]["stream"])
         for sl in slots[1:]:
