@@ -55,6 +55,8 @@ def parse():
                         "log-uniform size in [2^8, 2^20] with uint32 payloads per step")
     p.add_argument("--arrays", type=int, default=20000)
     p.add_argument("--retune", action="store_true", help="batched: re-run the autotuner")
+    p.add_argument("--tuned-out", default="", help="batched: where --retune writes its table "
+                   "(default: the package's tuned table)")
     p.add_argument("--requests", type=int, default=100, help="serve: requests per arrival-rate run")
     p.add_argument("--slots", type=int, default=4, help="serve: launch slots (streams) of the server")
     p.add_argument("--small-max", type=int, default=1 << 20,
@@ -285,9 +287,9 @@ def run_batched(args):
         table, tile = {int(c): int(k) for c, k in res["class_fanout"].items()}, int(res["tile_items"])
         tuned_from = "autotuner run in this process"
         if rank == 0:
-            os.makedirs(os.path.dirname(TUNED), exist_ok=True)
-            autotune.save(res, os.path.join(ROOT, "gpurun_out", "batched_u32_pairs.json")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else TUNED)
+            dest = args.tuned_out or TUNED
+            os.makedirs(os.path.dirname(os.path.abspath(dest)), exist_ok=True)
+            autotune.save(res, dest)
     mx = int(sizes.max())
     graph = mms.SegmentedGraph(work_k, off, work_v, kt=mms.KEY_U32, class_fanout=table, tile_items=tile,
                                max_segment_items=mx)
