@@ -63,6 +63,13 @@ def test_group_caps_and_large_requests():
     assert len(form_group(q, 1 << 20, 1 << 25, 4)) == 4                    # segment cap
 
 
+def test_group_without_coalescing():
+    """small_max = 0 (bench --small-max 0): every request is its own group."""
+    q = [req(i, 1000) for i in range(5)]
+    assert [r.rid for r in form_group(q, 0, 1 << 25, 64)] == [0]
+    assert [r.rid for r in form_group(q[1:], 0, 1 << 25, 64)] == [1]
+
+
 def test_poisson_arrivals_rate():
     t = poisson_arrivals(20000, 250.0, 3)
     assert np.all(np.diff(t) > 0)
