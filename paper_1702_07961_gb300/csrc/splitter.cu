@@ -4,7 +4,7 @@
 
 namespace mms {
 
-template <typename KeyT, int W>
+template <typename KeyT, int W, typename Idx>
 __global__ void __launch_bounds__(128)
     splitter_kernel(const KeyT* __restrict__ in, long long n, long long run_len, int K,
                     long long S, long long tpg, long long ntiles, long long* __restrict__ table) {
@@ -13,7 +13,7 @@ __global__ void __launch_bounds__(128)
   const unsigned gm = W == 32 ? 0xffffffffu : (((1u << W) - 1u) << gb);
   const long long t = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / W) + gb / W;
   if (t >= ntiles) return;                        // uniform over the lane group
-  splitter_row<KeyT, W>(in, n, run_len, K, S, t / tpg, t % tpg, table + t * K, gm, gb);
+  splitter_row<KeyT, W, Idx>(in, n, run_len, K, S, t / tpg, t % tpg, table + t * K, gm, gb);
 }
 
 template <typename KeyT, int W>
@@ -21,8 +21,13 @@ static void launch_w(const void* in, long long n, long long run_len, int K, long
                      long long ntiles, long long* table, cudaStream_t s) {
   const long long per_block = 4 * (32 / W);       // 4 warps of 32 / W tiles each
   const unsigned grid = (unsigned)((ntiles + per_block - 1) / per_block);
-  splitter_kernel<KeyT, W><<<grid, 128, 0, s>>>(static_cast<const KeyT*>(in), n, run_len, K, S, tpg,
-                                                ntiles, table);
+  // 32-bit counts and positions while no probe can pass 2^31 (n < 2^30)
+  if (n < (1ll << 30))
+    splitter_kernel<KeyT, W, int><<<grid, 128, 0, s>>>(static_cast<const KeyT*>(in), n, run_len, K, S,
+                                                       tpg, ntiles, table);
+  else
+    splitter_kernel<KeyT, W, long long><<<grid, 128, 0, s>>>(static_cast<const KeyT*>(in), n, run_len,
+                                                             K, S, tpg, ntiles, table);
 }
 
 // One output tile per warp (W = 32).  Packing 32 / W tiles into a warp's lane

@@ -31,8 +31,8 @@ struct Item {
   bool pad;
 };
 
-template <typename KeyT>
-__device__ __forceinline__ Item<KeyT> load_item(const KeyT* run, long long len, long long pos) {
+template <typename KeyT, typename Idx>
+__device__ __forceinline__ Item<KeyT> load_item(const KeyT* run, Idx len, Idx pos) {
   Item<KeyT> it;
   it.pad = pos >= len;
   it.key = it.pad ? KeyT(0) : run[pos];
@@ -113,8 +113,10 @@ __device__ __forceinline__ Item<KeyT> shfl_item(unsigned gm, const Item<KeyT>& i
 // Pivots of output tile j of group g, found by one lane group of W >= K lanes
 // (gm: its lanes, gb: its first lane; lane gb + r handles run r): row[r]
 // receives the number of items of run r among the group's first j * S
-// outputs.  Arguments are uniform over the lane group.
-template <typename KeyT, int W>
+// outputs.  Arguments are uniform over the lane group.  Idx is the type of
+// the counts and positions of the search: int when n < 2^30 (every position
+// probed stays below 2n), long long otherwise.
+template <typename KeyT, int W, typename Idx = long long>
 __device__ __forceinline__ void splitter_row(const KeyT* __restrict__ in, long long n,
                                              long long run_len, int K, long long S, long long g,
                                              long long j, long long* __restrict__ row,
@@ -123,27 +125,27 @@ __device__ __forceinline__ void splitter_row(const KeyT* __restrict__ in, long l
   const int rr = lane - gb;                     // run of this lane
   const bool act = rr < K;
   const long long rstart = g * run_len * K + (long long)rr * run_len;
-  long long rlen = n - rstart;
-  rlen = rlen < 0 ? 0 : (rlen > run_len ? run_len : rlen);
-  if (!act) rlen = 0;
+  long long rlen64 = n - rstart;
+  rlen64 = rlen64 < 0 ? 0 : (rlen64 > run_len ? run_len : rlen64);
+  const Idx rlen = act ? (Idx)rlen64 : Idx(0);
   const KeyT* run = in + (act ? rstart : 0);
-  const long long k = j * S;
+  const Idx k = (Idx)(j * S);
 
-  long long d = 0;            // selected samples of this run at the current stride
+  Idx d = 0;                  // selected samples of this run at the current stride
   Item<KeyT> e{KeyT(0), false};  // the d-th sample (position d*s-1) when d >= 1
-  const int T = 64 - __clzll(k);
+  const int T = 64 - __clzll((long long)k);
   for (int lev = T; lev >= 1; --lev) {
     const int sh = lev - 1;                     // s2 = 2^sh
-    const long long kp = k >> sh;
-    const long long dd = 2 * d;
+    const Idx kp = k >> sh;
+    const Idx dd = 2 * d;
     Item<KeyT> o = load_item(run, rlen, ((dd + 1) << sh) - 1);
     Item<KeyT> z{KeyT(0), false};
     if (d >= 1) z = load_item(run, rlen, ((dd - 1) << sh) - 1);
     // Items to drop: (sum of the lanes' 2d + 1) - kp, which lies in [0, K];
     // one 32-bit warp reduction, exact modulo 2^32 since the result is small.
     const unsigned dsum = __reduce_add_sync(gm, act ? (unsigned)d : 0u);
-    const long long jrem = (int)(2u * dsum + (unsigned)K - (unsigned)kp);
-    long long cnt = dd + 1;
+    const Idx jrem = (int)(2u * dsum + (unsigned)K - (unsigned)kp);
+    Idx cnt = dd + 1;
 
     // Candidates above every selected item are dropped first, in one step.
     const bool hasZ = act && d >= 1;
@@ -154,8 +156,8 @@ __device__ __forceinline__ void splitter_row(const KeyT* __restrict__ in, long l
       above = act && (lane == mz || before_cross(zmax, mz, o, lane));
     }
     const unsigned abovem = __ballot_sync(gm, above);
-    const long long u = __popc(abovem);
-    long long pops;
+    const Idx u = __popc(abovem);
+    Idx pops;
     if (u <= jrem) {
       if (above) cnt = dd;
       pops = jrem - u;
@@ -166,7 +168,7 @@ __device__ __forceinline__ void splitter_row(const KeyT* __restrict__ in, long l
     }
     // Remaining drops one at a time from the largest current top.
     Item<KeyT> top = (cnt == dd + 1) ? o : e;
-    for (long long p = 0; p < pops; ++p) {
+    for (Idx p = 0; p < pops; ++p) {
       const int w = grp_argmax(gm, act && cnt >= 1, top);
       if (lane == w) {
         cnt -= 1;
