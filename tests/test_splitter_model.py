@@ -11,14 +11,20 @@ probes, the same "drop every candidate above all selected items first" step,
 the same pops from the largest top -- and checks:
   * the result equals brute force on small inputs with many duplicates;
   * every level drops K - 1 or K items, the range that lets the kernel count
-    them with one 32-bit warp reduction modulo 2^32.
+    them with one 32-bit warp reduction modulo 2^32;
+  * every probed position lies below 2k, so for n < 2^30 the kernel's 32-bit
+    counts and positions cannot overflow.
 """
 import numpy as np
 import pytest
 
 
+PROBES = []
+
+
 def item(run, pos):
     """(pad, key): positions past the run's end are pads, after every real item."""
+    PROBES.append(pos)
     return (True, 0) if pos >= len(run) else (False, int(run[pos]))
 
 
@@ -113,7 +119,10 @@ def test_splitter_model_matches_brute_force(K, vals):
             if k < 0:
                 continue
             drops = []
+            PROBES.clear()
             assert splitter_model(runs, k, drops) == brute(runs, k), (trial, lens, k)
+            # every probe lies below 2k: the kernel's 32-bit variant (n < 2^30) cannot overflow
+            assert all(0 <= p < 2 * k for p in PROBES), (k, max(PROBES, default=0))
             # every level drops K - 1 or K items (one warp reduction, exact modulo 2^32)
             assert all(K - 1 <= j <= K for j, _ in drops), drops
 
