@@ -10,13 +10,20 @@
  *     chip without shared-memory bank conflicts (Sec. 4.2).
  *
  * Conventions for every entry point:
- *   - Pointers named d_* are device pointers the caller owns; they must be
- *     16-byte aligned (any cudaMalloc / PyTorch allocation is).  `stream` is a
- *     cudaStream_t (NULL = the legacy default stream).
- *   - Calls are asynchronous on `stream`: they return once the work is queued.
+ *   - Pointers named d_* are device pointers the caller owns.  Key and value
+ *     arrays need only the alignment of their element (4 bytes for u32, f32
+ *     and values, 8 bytes for u64), so a tensor slice at any element offset
+ *     is accepted; arrays on the 16-byte grid take the vectorised paths.
+ *     Workspaces must be 16-byte aligned (the batched sort's 256-byte
+ *     aligned).  `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - Calls are asynchronous on `stream`: they return once the work is queued,
+ *     also when the library allocates the workspace itself (stream-ordered).
  *     Argument errors are reported synchronously by the return value.
- *     Device-side errors (a bounded wait that ran out) are recorded in the
- *     workspace status word and read back by mms_workspace_status().
+ *     Device-side errors (a bounded wait that ran out, a failed consistency
+ *     check) are recorded in the status word of the call's workspace, which
+ *     every call clears first, and read back by mms_workspace_status(); a
+ *     call whose workspace the library allocated forwards its status word to
+ *     a per-device word that mms_stream_status() reads.
  *   - Sorting is ascending and stable: equal keys keep their input order and
  *     32-bit values move with their keys.
  *   - Key types: 32- and 64-bit unsigned integers (the paper's 4- and 8-byte
@@ -62,8 +69,16 @@ typedef struct {
                         for 4-byte keys, 2048 or 4096 for 8-byte keys */
   int merge_tile_items; /* output tile of the merge rounds: 0 = tile_items; else a multiple
                         of 1024 from 4096 (2048 for 8-byte keys) up to tile_items */
-  int reserved[2];
+  int test_flags;    /* test hooks, 0 in normal use.  MMS_TEST_STAGING_TIMEOUT: every merge
+                        CTA of mms_sort_keys_ex, once its staged inputs have all arrived,
+                        also waits (about a millisecond) on a barrier that no copy
+                        completes, then records MMS_ERR_TIMEOUT and stops: the device-side
+                        failure path, with nothing left in flight.  The output is then
+                        unspecified. */
+  int reserved;
 } mms_options;
+
+#define MMS_TEST_STAGING_TIMEOUT 1
 
 /* Bytes of workspace mms_sort_keys / mms_sort_pairs need for n keys: one
  * ping-pong copy of the keys (and values), the pivot table of the largest
@@ -71,9 +86,12 @@ typedef struct {
 size_t mms_sort_workspace_bytes(mms_key_type kt, size_t n, int with_values);
 
 /* Sorts n keys of type kt at d_keys in place (from the caller's view).
- * d_ws: workspace of at least mms_sort_workspace_bytes(kt, n, 0) bytes, or
- * NULL to let the library allocate one stream-ordered (cudaMallocAsync) and
- * free it after the sort.  n = 0 and n = 1 are no-ops. */
+ * d_ws: workspace of at least mms_sort_workspace_bytes(kt, n, 0) bytes (any
+ * contents: its status word is cleared on `stream` first), or NULL to let the
+ * library allocate one stream-ordered (cudaMallocAsync) and free it after the
+ * sort; the call then still returns without waiting for the GPU, and its
+ * device-side status goes to the word mms_stream_status() reads.  n = 0 and
+ * n = 1 are no-ops. */
 mms_status mms_sort_keys(mms_key_type kt, void* d_keys, size_t n, void* d_ws, size_t ws_bytes,
                          void* stream);
 mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws, size_t ws_bytes,
@@ -100,6 +118,13 @@ mms_status mms_sort_pairs_ex(mms_key_type kt, void* d_keys, uint32_t* d_values, 
 /* Reads (synchronising with `stream`) and clears the workspace status word:
  * MMS_OK, MMS_ERR_TIMEOUT or MMS_ERR_INTERNAL. */
 mms_status mms_workspace_status(void* d_ws, size_t ws_bytes, void* stream);
+
+/* Status of the sorts that ran without a caller workspace (d_ws == NULL) on
+ * the current device: waits for `stream`, then returns and clears the first
+ * device-side error any of them recorded since the last call (MMS_OK,
+ * MMS_ERR_TIMEOUT or MMS_ERR_INTERNAL).  The word is per device, shared by
+ * all streams: wait for the other streams' sorts before relying on it. */
+mms_status mms_stream_status(void* stream);
 
 /* ---- the hot-path steps one by one (for parity tests and profiling) -------- */
 
@@ -180,9 +205,10 @@ int mms_segmented_rounds(mms_key_type kt, size_t max_segment_items, int with_val
 
 /* Sorts every segment of d_keys in place; with d_values (total_n < 2^32) the
  * 32-bit values move with their keys (8-byte keys: two stable passes, as for
- * mms_sort_pairs).  d_ws (256-byte
- * aligned, mms_segmented_workspace_bytes) is required.  Asynchronous on
- * `stream`. */
+ * mms_sort_pairs).  d_keys and d_values must be 16-byte aligned (the
+ * segments inside may start at any item).  d_ws (256-byte aligned,
+ * mms_segmented_workspace_bytes) is required; its status word is cleared
+ * first.  Asynchronous on `stream`. */
 mms_status mms_segmented_sort(mms_key_type kt, void* d_keys, uint32_t* d_values,
                               const uint64_t* d_offsets, size_t num_segments, size_t total_n,
                               void* d_ws, size_t ws_bytes, void* stream,
@@ -216,13 +242,22 @@ void mms_graph_destroy(mms_graph g);
  *   - The first call on a device looks up that device's copy of the array
  *     (cudaGetSymbolAddress) with the device current; make that first call
  *     before any stream capture.
+ *   - The address is cached per device and per CUDA context: after a
+ *     device reset the next call looks it up again in the new context.
  *   - All calls share the one array: calls whose work overlaps on the GPU
  *     (different streams, no ordering between them) race and corrupt each
  *     other's results.  Order them on one stream or with events.
- *   - Device-side error flags land in the array and are not reported. */
+ *   - Every call clears the array's status word first; device-side errors of
+ *     the latest call are read back with mms_noalloc_status(). */
 #define MMS_NOALLOC_MAX_KEYS_4B ((size_t)1 << 20)
 #define MMS_NOALLOC_MAX_KEYS_8B ((size_t)1 << 19)
 mms_status mms_sort_keys_noalloc(mms_key_type kt, void* d_keys, size_t n, void* stream);
+
+/* Device-side status of the latest mms_sort_keys_noalloc call on the current
+ * device, as mms_workspace_status reports it for a caller's workspace: waits
+ * for `stream`, returns MMS_OK, MMS_ERR_TIMEOUT or MMS_ERR_INTERNAL, and
+ * clears the word.  Allocates nothing. */
+mms_status mms_noalloc_status(void* stream);
 
 /* ---- diagnostics ----------------------------------------------------------- */
 

@@ -18,7 +18,8 @@ import threading
 
 __all__ = ["load", "KEY_U32", "KEY_U64", "KEY_F32", "key_type_of", "sort_keys", "sort_pairs",
            "workspace_bytes", "tile_items", "plan", "tile_sort", "splitter_rows", "splitter",
-           "merge_pass", "workspace_status", "MMSError", "sort_keys_noalloc", "NOALLOC_MAX_KEYS",
+           "merge_pass", "workspace_status", "stream_status", "MMSError", "sort_keys_noalloc",
+           "noalloc_status", "NOALLOC_MAX_KEYS", "TEST_STAGING_TIMEOUT",
            "segmented_workspace_bytes", "segmented_rounds", "segmented_sort", "SegmentedGraph"]
 
 KEY_U32, KEY_U64, KEY_F32 = 0, 1, 2
@@ -39,7 +40,13 @@ class MMSError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("fanout", ctypes.c_int), ("num_events", ctypes.c_int),
                 ("events", ctypes.POINTER(ctypes.c_void_p)), ("tile_items", ctypes.c_int),
-                ("merge_tile_items", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("merge_tile_items", ctypes.c_int), ("test_flags", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
+# mms_options.test_flags: a test hook that makes every merge CTA's extra
+# bounded wait run out (MMS_TEST_STAGING_TIMEOUT).
+TEST_STAGING_TIMEOUT = 1
 
 
 class _SegOptions(ctypes.Structure):
@@ -71,6 +78,10 @@ def load() -> ctypes.CDLL:
         L.mms_sort_pairs_ex.restype = i32
         L.mms_workspace_status.argtypes = [vp, sz, vp]
         L.mms_workspace_status.restype = i32
+        L.mms_stream_status.argtypes = [vp]
+        L.mms_stream_status.restype = i32
+        L.mms_noalloc_status.argtypes = [vp]
+        L.mms_noalloc_status.restype = i32
         L.mms_tile_items.argtypes = [i32]
         L.mms_tile_items.restype = sz
         L.mms_plan.argtypes = [i32, sz, ctypes.POINTER(_Options), ctypes.POINTER(ctypes.c_int), i32]
@@ -135,11 +146,13 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
-def _opts(fanout: int, events=None, stream=None, tile_items: int = 0, merge_tile_items: int = 0):
+def _opts(fanout: int, events=None, stream=None, tile_items: int = 0, merge_tile_items: int = 0,
+          test_flags: int = 0):
     o = _Options()
     o.fanout = int(fanout)
     o.tile_items = int(tile_items)
     o.merge_tile_items = int(merge_tile_items)
+    o.test_flags = int(test_flags)
     if events:
         for e in events:
             if not e.cuda_event:          # torch creates the CUDA event on first record
@@ -171,17 +184,18 @@ def plan(kt: int, n: int, fanout: int = 0, tile_items: int = 0, pairs: bool = Fa
 
 
 def sort_keys(keys, fanout: int = 0, workspace=None, stream=None, kt: int | None = None, events=None,
-              tile_items: int = 0, merge_tile_items: int = 0):
+              tile_items: int = 0, merge_tile_items: int = 0, test_flags: int = 0):
     """Sorts a contiguous CUDA tensor of keys in place; returns it.
 
     ``events``: optional list of ``torch.cuda.Event(enable_timing=True)``; the
     library records them before the first kernel and after each kernel.
+    ``test_flags``: test hooks (``TEST_STAGING_TIMEOUT``), 0 in normal use.
     """
     assert keys.is_cuda and keys.is_contiguous()
     kt = key_type_of(keys) if kt is None else kt
     n = keys.numel()
     ws_ptr, ws_len = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
-    o = _opts(fanout, events, stream, tile_items, merge_tile_items)
+    o = _opts(fanout, events, stream, tile_items, merge_tile_items, test_flags)
     _check(load().mms_sort_keys_ex(kt, _ptr(keys), n, ws_ptr, ws_len, _stream_handle(stream), ctypes.byref(o)))
     return keys
 
@@ -203,6 +217,12 @@ def workspace_status(workspace, stream=None) -> None:
     """Raises MMSError if a kernel recorded a device-side error in the workspace."""
     _check(load().mms_workspace_status(_ptr(workspace), workspace.numel() * workspace.element_size(),
                                        _stream_handle(stream)))
+
+
+def stream_status(stream=None) -> None:
+    """Raises MMSError if a sort that ran without a caller workspace on the
+    current device recorded a device-side error (waits for ``stream``)."""
+    _check(load().mms_stream_status(_stream_handle(stream)))
 
 
 def tile_sort(inp, out=None, stream=None, kt: int | None = None):
@@ -253,10 +273,14 @@ def sort_keys_noalloc(keys, stream=None, kt: int | None = None):
     n = keys.numel()
     if n > NOALLOC_MAX_KEYS[kt]:
         raise ValueError(f"sort_keys_noalloc takes at most {NOALLOC_MAX_KEYS[kt]} keys of this type, got {n}")
-    status = load().mms_sort_keys_noalloc(kt, _ptr(keys), n, _stream_handle(stream))
-    if status != 0:
-        raise MMSError(status, f"mms_sort_keys_noalloc failed: {load().mms_status_string(status).decode()}")
+    _check(load().mms_sort_keys_noalloc(kt, _ptr(keys), n, _stream_handle(stream)))
     return keys
+
+
+def noalloc_status(stream=None) -> None:
+    """Raises MMSError if the latest sort_keys_noalloc call on the current device
+    recorded a device-side error (waits for ``stream``); allocates nothing."""
+    _check(load().mms_noalloc_status(_stream_handle(stream)))
 
 
 # ---- batched (segmented) sorting ------------------------------------------------------

@@ -27,6 +27,9 @@ mms_status cuda_fail(cudaError_t e, const char* where) {
 int key_bytes_of(mms_key_type kt) { return kt == MMS_KEY_U64 ? 8 : 4; }
 bool valid_kt(int kt) { return kt == MMS_KEY_U32 || kt == MMS_KEY_U64 || kt == MMS_KEY_F32; }
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+// Key and value arrays need only their element's alignment; the kernels take
+// their vectorised paths on the parts that lie on the 16-byte grid.
+bool aligned_to(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
 
 constexpr size_t kStatusBytes = 256;
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -175,6 +178,53 @@ mms_status check_launch(cudaError_t e, const char* where) {
   return e == cudaSuccess ? MMS_OK : cuda_fail(e, where);
 }
 
+// Status of the sorts whose workspace the library allocated: before the
+// workspace is freed, its status word is forwarded here (the first error
+// since the last mms_stream_status wins).  One word per device.
+__device__ int g_stream_status;
+
+__global__ void forward_status_kernel(const int* __restrict__ ws_status) {
+  const int w = *ws_status;
+  if (w != 0) atomicCAS(&g_stream_status, 0, w);
+}
+
+// Allocates a workspace stream-ordered and clears its status word.
+mms_status alloc_workspace(void** d_ws, size_t bytes, cudaStream_t s) {
+  cudaError_t e = cudaMallocAsync(d_ws, bytes, s);
+  if (e != cudaSuccess) return fail(MMS_ERR_NO_MEMORY, "cudaMallocAsync of the workspace failed%s");
+  e = cudaMemsetAsync(*d_ws, 0, kStatusBytes, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(*d_ws, s);
+    return cuda_fail(e, "workspace init");
+  }
+  return MMS_OK;
+}
+
+// Ends a sort on a library-allocated workspace without waiting for it: the
+// status word goes to the per-device word, then the workspace is freed, both
+// in stream order.
+mms_status release_workspace(void* d_ws, cudaStream_t s, mms_status st) {
+  forward_status_kernel<<<1, 1, 0, s>>>(static_cast<const int*>(d_ws));
+  const cudaError_t e1 = cudaGetLastError();
+  const cudaError_t e2 = cudaFreeAsync(d_ws, s);
+  if (st == MMS_OK && e1 != cudaSuccess) st = cuda_fail(e1, "status forwarding");
+  if (st == MMS_OK && e2 != cudaSuccess) st = cuda_fail(e2, "workspace release");
+  return st;
+}
+
+// Clears the status word of a caller's workspace on the stream, so that a
+// stale or uninitialised word never reads as this call's error.
+mms_status clear_status(void* d_ws, cudaStream_t s) {
+  const cudaError_t e = cudaMemsetAsync(d_ws, 0, sizeof(int), s);
+  return e == cudaSuccess ? MMS_OK : cuda_fail(e, "status word");
+}
+
+mms_status status_of_word(int word) {
+  if (word == mms::kDevErrTimeout) return fail(MMS_ERR_TIMEOUT, "a device wait timed out%s");
+  if (word != 0) return fail(MMS_ERR_INTERNAL, "device consistency check failed%s");
+  return MMS_OK;
+}
+
 }  // namespace
 
 namespace mms {
@@ -228,16 +278,31 @@ mms_status mms_workspace_status(void* d_ws, size_t ws_bytes, void* stream) {
   if (e == cudaSuccess && word != 0) e = cudaMemsetAsync(d_ws, 0, sizeof word, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "mms_workspace_status");
-  if (word == mms::kDevErrTimeout) return fail(MMS_ERR_TIMEOUT, "a device wait timed out%s");
-  if (word != 0) return fail(MMS_ERR_INTERNAL, "device consistency check failed%s");
-  return MMS_OK;
+  return status_of_word(word);
+}
+
+mms_status mms_stream_status(void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  int word = 0;
+  const int zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(&word, g_stream_status, sizeof word, 0,
+                                            cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && word != 0)
+    e = cudaMemcpyToSymbolAsync(g_stream_status, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "mms_stream_status");
+  return status_of_word(word);
 }
 
 mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws, size_t ws_bytes,
                             void* stream, const mms_options* opt) {
   if (!valid_kt(kt)) return fail(MMS_ERR_INVALID_ARG, "unknown key type%s");
   if (n <= 1) return MMS_OK;
-  if (!d_keys || !aligned16(d_keys)) return fail(MMS_ERR_INVALID_ARG, "keys pointer null or not 16-byte aligned%s");
+  if (!d_keys || !aligned_to(d_keys, (size_t)key_bytes_of(kt)))
+    return fail(MMS_ERR_INVALID_ARG, "keys pointer null or not aligned to the key size%s");
+  if (opt && (opt->test_flags & ~MMS_TEST_STAGING_TIMEOUT))
+    return fail(MMS_ERR_INVALID_ARG, "unknown test flag%s");
   if (opt && opt->fanout != 0 && (opt->fanout < 2 || opt->fanout > mms::kMaxFanout))
     return fail(MMS_ERR_INVALID_ARG, "fanout must be 0 or in 2..32%s");
   const int kb = key_bytes_of(kt);
@@ -256,15 +321,16 @@ mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws,
   if (d_ws) {
     if (!aligned16(d_ws)) return fail(MMS_ERR_INVALID_ARG, "workspace not 16-byte aligned%s");
     if (ws_bytes < L.total) return fail(MMS_ERR_NO_MEMORY, "workspace smaller than mms_sort_workspace_bytes()%s");
+    const mms_status cs = clear_status(d_ws, s);
+    if (cs != MMS_OK) return cs;
   } else {
-    cudaError_t e = cudaMallocAsync(&d_ws, L.total, s);
-    if (e != cudaSuccess) return fail(MMS_ERR_NO_MEMORY, "cudaMallocAsync of the workspace failed%s");
-    e = cudaMemsetAsync(d_ws, 0, kStatusBytes, s);
-    if (e != cudaSuccess) { cudaFreeAsync(d_ws, s); return cuda_fail(e, "workspace init"); }
+    const mms_status as = alloc_workspace(&d_ws, L.total, s);
+    if (as != MMS_OK) return as;
     owned = true;
   }
   unsigned char* ws = static_cast<unsigned char*>(d_ws);
   int* dev_err = reinterpret_cast<int*>(ws);
+  const bool test_timeout = opt && (opt->test_flags & MMS_TEST_STAGING_TIMEOUT);
   void* tmp = ws + L.keys_off;
   long long* table = reinterpret_cast<long long*>(ws + L.table_off);
 
@@ -292,7 +358,8 @@ mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws,
     mark();
     if (st != MMS_OK) break;
     st = check_launch(mms::launch_merge_pass(kb, tw, Sm, is_f32 && r == rounds - 1, cur, other,
-                                             (long long)n, run_len, K[r], table, dev_err, s),
+                                             (long long)n, run_len, K[r], table, dev_err, s,
+                                             test_timeout),
                       "merge_pass");
     mark();
     void* t = cur;
@@ -300,16 +367,7 @@ mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws,
     other = t;
     run_len *= K[r];
   }
-  if (owned) {
-    // A device-side error would be lost with the workspace: surface it now.
-    int word = 0;
-    cudaError_t e = cudaMemcpyAsync(&word, dev_err, sizeof word, cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(d_ws, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (st == MMS_OK && e != cudaSuccess) st = cuda_fail(e, "sort");
-    if (st == MMS_OK && word == mms::kDevErrTimeout) st = fail(MMS_ERR_TIMEOUT, "a device wait timed out%s");
-    else if (st == MMS_OK && word != 0) st = fail(MMS_ERR_INTERNAL, "device consistency check failed%s");
-  }
+  if (owned) st = release_workspace(d_ws, s, st);
   return st;
 }
 
@@ -375,23 +433,25 @@ mms_status mms_sort_pairs_ex(mms_key_type kt, void* d_keys, uint32_t* d_values, 
   if (!valid_kt(kt)) return fail(MMS_ERR_INVALID_ARG, "unknown key type%s");
   if (n <= 1) return MMS_OK;
   if (n > 0xFFFFFFFEull) return fail(MMS_ERR_UNSUPPORTED, "key-value sorting takes fewer than 2^32 items%s");
-  if (!d_keys || !d_values || !aligned16(d_keys) || !aligned16(d_values))
-    return fail(MMS_ERR_INVALID_ARG, "keys/values pointer null or not 16-byte aligned%s");
+  if (!d_keys || !d_values || !aligned_to(d_keys, (size_t)key_bytes_of(kt)) ||
+      !aligned_to(d_values, sizeof(uint32_t)))
+    return fail(MMS_ERR_INVALID_ARG, "keys/values pointer null or not aligned to the element size%s");
   if (opt && opt->fanout != 0 && (opt->fanout < 2 || opt->fanout > mms::kMaxFanout))
     return fail(MMS_ERR_INVALID_ARG, "fanout must be 0 or in 2..32%s");
   if (opt && opt->tile_items != 0 && opt->tile_items != 2048 && opt->tile_items != 4096)
     return fail(MMS_ERR_INVALID_ARG, "tile_items of a key-value sort must be 0, 2048 or 4096%s");
+  if (opt && opt->test_flags != 0) return fail(MMS_ERR_INVALID_ARG, "test flags apply to mms_sort_keys_ex only%s");
   const WsLayout L = ws_layout(kt, n, 1);
   cudaStream_t s = (cudaStream_t)stream;
   bool owned = false;
   if (d_ws) {
     if (!aligned16(d_ws)) return fail(MMS_ERR_INVALID_ARG, "workspace not 16-byte aligned%s");
     if (ws_bytes < L.total) return fail(MMS_ERR_NO_MEMORY, "workspace smaller than mms_sort_workspace_bytes()%s");
+    const mms_status cs = clear_status(d_ws, s);
+    if (cs != MMS_OK) return cs;
   } else {
-    cudaError_t e = cudaMallocAsync(&d_ws, L.total, s);
-    if (e != cudaSuccess) return fail(MMS_ERR_NO_MEMORY, "cudaMallocAsync of the workspace failed%s");
-    e = cudaMemsetAsync(d_ws, 0, kStatusBytes, s);
-    if (e != cudaSuccess) { cudaFreeAsync(d_ws, s); return cuda_fail(e, "workspace init"); }
+    const mms_status as = alloc_workspace(&d_ws, L.total, s);
+    if (as != MMS_OK) return as;
     owned = true;
   }
   unsigned char* ws = static_cast<unsigned char*>(d_ws);
@@ -420,15 +480,7 @@ mms_status mms_sort_pairs_ex(mms_key_type kt, void* d_keys, uint32_t* d_values, 
                                                     (long long)n, s),
                         "key-value permutation (8-byte keys)");
   }
-  if (owned) {
-    int word = 0;
-    cudaError_t e = cudaMemcpyAsync(&word, dev_err, sizeof word, cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(d_ws, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (st == MMS_OK && e != cudaSuccess) st = cuda_fail(e, "sort");
-    if (st == MMS_OK && word == mms::kDevErrTimeout) st = fail(MMS_ERR_TIMEOUT, "a device wait timed out%s");
-    else if (st == MMS_OK && word != 0) st = fail(MMS_ERR_INTERNAL, "device consistency check failed%s");
-  }
+  if (owned) st = release_workspace(d_ws, s, st);
   return st;
 }
 
@@ -440,10 +492,10 @@ mms_status mms_sort_pairs(mms_key_type kt, void* d_keys, uint32_t* d_values, siz
 mms_status mms_tile_sort(mms_key_type kt, const void* d_in, void* d_out, size_t n, void* stream) {
   if (!valid_kt(kt)) return fail(MMS_ERR_INVALID_ARG, "unknown key type%s");
   if (n == 0) return MMS_OK;
-  if (!d_in || !d_out || !aligned16(d_in) || !aligned16(d_out))
-    return fail(MMS_ERR_INVALID_ARG, "buffers null or not 16-byte aligned%s");
-  const bool f = kt == MMS_KEY_F32;
   const int kb = key_bytes_of(kt);
+  if (!d_in || !d_out || !aligned_to(d_in, (size_t)kb) || !aligned_to(d_out, (size_t)kb))
+    return fail(MMS_ERR_INVALID_ARG, "buffers null or not aligned to the key size%s");
+  const bool f = kt == MMS_KEY_F32;
   return check_launch(mms::launch_tile_sort(kb, mms::default_tile_warps(kb), f, f, d_in, d_out, (long long)n,
                                             (cudaStream_t)stream), "tile_sort");
 }
@@ -470,8 +522,9 @@ mms_status mms_splitter(mms_key_type kt, const void* d_in, size_t n, size_t run_
   mms_status st = check_round_args(kt, run_len, K);
   if (st != MMS_OK) return st;
   if (n == 0) return MMS_OK;
-  if (!d_in || !d_table || !aligned16(d_in)) return fail(MMS_ERR_INVALID_ARG, "null or misaligned buffer%s");
   const int kb = key_bytes_of(kt);
+  if (!d_in || !d_table || !aligned_to(d_in, (size_t)kb) || !aligned_to(d_table, sizeof(int64_t)))
+    return fail(MMS_ERR_INVALID_ARG, "null or misaligned buffer%s");
   return check_launch(mms::launch_splitter(kb, 1024ll * mms::default_tile_warps(kb), d_in, (long long)n,
                                            (long long)run_len,
                                            K, reinterpret_cast<long long*>(d_table),
@@ -484,13 +537,15 @@ mms_status mms_merge_pass(mms_key_type kt, const void* d_in, void* d_out, size_t
   mms_status st = check_round_args(kt, run_len, K);
   if (st != MMS_OK) return st;
   if (n == 0) return MMS_OK;
-  if (!d_in || !d_out || !d_table || !aligned16(d_in) || !aligned16(d_out))
-    return fail(MMS_ERR_INVALID_ARG, "null or misaligned buffer%s");
   const size_t kb = (size_t)key_bytes_of(kt);
+  if (!d_in || !d_out || !d_table || !aligned_to(d_in, kb) || !aligned_to(d_out, kb) ||
+      !aligned_to(d_table, sizeof(int64_t)))
+    return fail(MMS_ERR_INVALID_ARG, "null or misaligned buffer%s");
   const char* a = static_cast<const char*>(d_in);
   const char* b = static_cast<const char*>(d_out);
   if (a < b + n * kb && b < a + n * kb) return fail(MMS_ERR_INVALID_ARG, "input and output overlap%s");
-  if (d_ws && ws_bytes < kStatusBytes) return fail(MMS_ERR_INVALID_ARG, "workspace too small%s");
+  if (d_ws && (ws_bytes < kStatusBytes || !aligned16(d_ws)))
+    return fail(MMS_ERR_INVALID_ARG, "workspace too small or not 16-byte aligned%s");
   int* dev_err = d_ws ? static_cast<int*>(d_ws) : nullptr;
   return check_launch(mms::launch_merge_pass((int)kb, mms::default_tile_warps((int)kb),
                                              1024ll * mms::default_tile_warps((int)kb), false, d_in,

@@ -12,22 +12,25 @@ template <typename KeyT, int WARPS, bool XOUT>
 __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
     merge_pass_kernel(const KeyT* __restrict__ in, KeyT* __restrict__ out, long long n,
                       long long run_len, int K, const long long* __restrict__ table,
-                      long long tpg, int S, int* dev_err) {
+                      long long tpg, int S, int* dev_err, int test_timeout) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int cap = MergeGeom<KeyT, WARPS>::cap(K);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + sizeof(KeyT) * 2 * (size_t)cap);
   const long long t = blockIdx.x;
   const unsigned tq = (unsigned)blockIdx.x / (unsigned)tpg;    // tiles and tpg fit in 32 bits
   const long long g = tq, j = (long long)((unsigned)blockIdx.x - tq * (unsigned)tpg);
-  if (threadIdx.x == 0) mbar_init(bar, 1);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    if (test_timeout) mbar_init(bar + 1, 1);   // the test hook's barrier (bar[1] is spare)
+  }
   merge_tile<KeyT, WARPS>(in, out, n, run_len, K, g, j, table + t * K, table + (t + 1) * K, XOUT,
-                          dev_err, smem_raw, bar, 0u, S);
+                          dev_err, smem_raw, bar, 0u, S, test_timeout != 0);
 }
 
 template <typename KeyT, int WARPS, bool XOUT>
 static cudaError_t launch_merge_t(long long S, const void* in, void* out, long long n,
                                   long long run_len, int K, const long long* table, int* dev_err,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, bool test_timeout) {
   const size_t smem = MergeGeom<KeyT, WARPS>::bytes(K);
   auto k = merge_pass_kernel<KeyT, WARPS, XOUT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -37,25 +40,27 @@ static cudaError_t launch_merge_t(long long S, const void* in, void* out, long l
   long long tpg = tiles_per_group(S, run_len, K);
   if (tpg > 0xFFFFFFFFll) tpg = 0xFFFFFFFFll;   // more than the grid: every tile is in group 0
   k<<<(unsigned)ntiles, WARPS * 32, smem, s>>>(static_cast<const KeyT*>(in), static_cast<KeyT*>(out),
-                                              n, run_len, K, table, tpg, (int)S, dev_err);
+                                              n, run_len, K, table, tpg, (int)S, dev_err,
+                                              test_timeout ? 1 : 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_merge_pass(int key_bytes, int tile_warps, long long S, bool xout, const void* in,
                               void* out, long long n, long long run_len, int K,
-                              const long long* table, int* dev_err, cudaStream_t s) {
+                              const long long* table, int* dev_err, cudaStream_t s,
+                              bool test_timeout) {
   if (n <= 0) return cudaSuccess;
   if (key_bytes == 4) {
     if (tile_warps == 8)
-      return xout ? launch_merge_t<uint32_t, 8, true>(S, in, out, n, run_len, K, table, dev_err, s)
-                  : launch_merge_t<uint32_t, 8, false>(S, in, out, n, run_len, K, table, dev_err, s);
+      return xout ? launch_merge_t<uint32_t, 8, true>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout)
+                  : launch_merge_t<uint32_t, 8, false>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout);
     if (tile_warps == 4)
-      return xout ? launch_merge_t<uint32_t, 4, true>(S, in, out, n, run_len, K, table, dev_err, s)
-                  : launch_merge_t<uint32_t, 4, false>(S, in, out, n, run_len, K, table, dev_err, s);
+      return xout ? launch_merge_t<uint32_t, 4, true>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout)
+                  : launch_merge_t<uint32_t, 4, false>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout);
     return cudaErrorInvalidValue;
   }
-  if (tile_warps == 4) return launch_merge_t<uint64_t, 4, false>(S, in, out, n, run_len, K, table, dev_err, s);
-  if (tile_warps == 2) return launch_merge_t<uint64_t, 2, false>(S, in, out, n, run_len, K, table, dev_err, s);
+  if (tile_warps == 4) return launch_merge_t<uint64_t, 4, false>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout);
+  if (tile_warps == 2) return launch_merge_t<uint64_t, 2, false>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout);
   return cudaErrorInvalidValue;
 }
 

@@ -304,13 +304,17 @@ __device__ __forceinline__ void merge_levels(KeyT* bufX, KeyT* bufY, const int* 
 // `xout` undoes the float transform on the tile's last level.  Returns false,
 // with the error recorded, when the CTA must stop (a pivot row fails its
 // check or the staging wait ran out); the decision is uniform over the CTA.
+// test_timeout (a test hook; bar[1] then holds an initialised mbarrier): once
+// the staged data has arrived, thread 0 also waits on bar[1] for 16 bytes no
+// copy delivers, with a limit of about a millisecond, so the CTA takes the
+// time-out path with no copy in flight.
 template <typename KeyT, int WARPS>
 __device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __restrict__ out,
                                            long long n, long long run_len, int K, long long g,
                                            long long j, const long long* __restrict__ lo_row,
                                            const long long* __restrict__ hi_row, bool xout,
                                            int* dev_err, unsigned char* smem_raw, uint64_t* bar,
-                                           unsigned phase, int S) {
+                                           unsigned phase, int S, bool test_timeout = false) {
   using G = MergeGeom<KeyT, WARPS>;
   const int cap = G::cap(K);
   KeyT* bufX = reinterpret_cast<KeyT*>(smem_raw);
@@ -333,7 +337,11 @@ __device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __
   // One thread polls the staging barrier; the others wait at the CTA barrier
   // (no issue slots spent polling), which also orders the staged data and the
   // plainly loaded items before every warp's reads.
-  const bool ok = (threadIdx.x == 0) ? mbar_wait_bounded(bar, phase) : true;
+  bool ok = (threadIdx.x == 0) ? mbar_wait_bounded(bar, phase) : true;
+  if (test_timeout && threadIdx.x == 0 && ok) {
+    mbar_arrive_expect_tx(bar + 1, 16u);
+    ok = mbar_wait_bounded(bar + 1, 0u, 2000000ll);
+  }
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) set_device_error(dev_err, kDevErrTimeout);
     return false;

@@ -524,9 +524,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned by
 }
 
 // Waits for phase `parity` of the barrier (each try_wait may suspend the
-// thread for up to 100 us), giving up after roughly two seconds; returns
-// false on time-out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+// thread for up to 100 us), giving up after `max_cycles` SM clocks (by
+// default about two seconds) or 2^26 tries; returns false on time-out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity,
+                                                  long long max_cycles = 4000000000ll) {
   const uint32_t addr = smem_u32addr(bar);
   const long long t0 = clock64();
   for (long long it = 0; it < (1ll << 26); ++it) {
@@ -538,7 +539,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
         : "r"(addr), "r"(parity), "r"(100000u)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > 4000000000ll) break;
+    if (clock64() - t0 > max_cycles) break;
   }
   return false;
 }

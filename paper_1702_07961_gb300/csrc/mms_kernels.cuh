@@ -69,10 +69,12 @@ cudaError_t launch_splitter(int key_bytes, long long S, const void* in, long lon
                             long long run_len, int K, long long* table, cudaStream_t s);
 
 // One K-way merge round driven by the splitter table; output tiles of S
-// items (a multiple of 1024, at most 1024 * tile_warps).
+// items (a multiple of 1024, at most 1024 * tile_warps).  test_timeout: the
+// test hook of mms_options.test_flags (every CTA's extra wait runs out).
 cudaError_t launch_merge_pass(int key_bytes, int tile_warps, long long S, bool xout, const void* in,
                               void* out, long long n, long long run_len, int K,
-                              const long long* table, int* dev_err, cudaStream_t s);
+                              const long long* table, int* dev_err, cudaStream_t s,
+                              bool test_timeout = false);
 
 // Records the detail message mms_last_error_detail() returns on this thread.
 void set_error_detail(const char* msg);

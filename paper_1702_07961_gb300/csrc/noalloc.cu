@@ -9,11 +9,13 @@
 // __device__ array of fixed size, so the call itself never allocates.  The
 // price is that every GPU that loads this library holds the array (about
 // 4 MiB) until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
 
 #include "../../include/mms.h"
+#include "mms_kernels.cuh"
 
 namespace {
 
@@ -27,37 +29,93 @@ constexpr int kMaxDevices = 64;
 // The scratch itself: one copy per device, alive until the process exits.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
+// The device address of the array, cached per device together with the CUDA
+// context it was looked up in: a device reset creates a new primary context,
+// and an address from the old one must not be used again.
+struct ScratchAddr {
+  CUcontext ctx;
+  void* ptr;
+};
 std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
+ScratchAddr g_scratch[kMaxDevices] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+bool g_ctx_fn_looked_up = false;
+
+// The current context, through the driver entry point the runtime hands out
+// (the library does not link the driver library itself).  nullptr when the
+// lookup fails; the cache then never matches and the address is looked up on
+// every call, which is correct, only slower.
+CUcontext current_context() {
+  if (!g_ctx_fn_looked_up) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+    g_ctx_fn_looked_up = true;
+  }
+  CUcontext c = nullptr;
+  if (g_ctx_get_current == nullptr || g_ctx_get_current(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
+
+mms_status fail_detail(mms_status s, const char* msg) {
+  mms::set_error_detail(msg);
+  return s;
+}
+
+// This device's address of the scratch array (set-up, with the device
+// current: the first call on a device, and again after a device reset).
+mms_status scratch_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return fail_detail(MMS_ERR_CUDA, "mms_sort_keys_noalloc: no usable current device");
+  std::lock_guard<std::mutex> lock(g_mu);
+  const CUcontext ctx = current_context();
+  ScratchAddr& e = g_scratch[dev];
+  if (e.ptr == nullptr || ctx == nullptr || e.ctx != ctx) {
+    void* p = nullptr;
+    const cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (err != cudaSuccess || p == nullptr)
+      return fail_detail(MMS_ERR_CUDA, "mms_sort_keys_noalloc: cudaGetSymbolAddress failed");
+    e.ptr = p;
+    e.ctx = current_context();   // the lookup has made the device's context current
+  }
+  *out = e.ptr;
+  return MMS_OK;
+}
 
 }  // namespace
 
 extern "C" mms_status mms_sort_keys_noalloc(mms_key_type kt, void* d_keys, size_t n,
                                             void* stream) {
-  if (kt != MMS_KEY_U32 && kt != MMS_KEY_U64 && kt != MMS_KEY_F32) return MMS_ERR_INVALID_ARG;
+  if (kt != MMS_KEY_U32 && kt != MMS_KEY_U64 && kt != MMS_KEY_F32)
+    return fail_detail(MMS_ERR_INVALID_ARG, "mms_sort_keys_noalloc: unknown key type");
   const size_t max_keys = (kt == MMS_KEY_U64) ? kNoAllocMaxKeys8 : kNoAllocMaxKeys4;
-  if (n > max_keys) return MMS_ERR_INVALID_ARG;   // beyond the fixed scratch: rejected, nothing queued
+  if (n > max_keys)   // beyond the fixed scratch: rejected, nothing queued
+    return fail_detail(MMS_ERR_INVALID_ARG,
+                       "mms_sort_keys_noalloc: n above MMS_NOALLOC_MAX_KEYS_4B / _8B");
   if (n <= 1) return MMS_OK;
-  if (mms_sort_workspace_bytes(kt, n, 0) > kNoAllocScratchBytes) return MMS_ERR_INTERNAL;
+  if (mms_sort_workspace_bytes(kt, n, 0) > kNoAllocScratchBytes)
+    return fail_detail(MMS_ERR_INTERNAL, "mms_sort_keys_noalloc: scratch smaller than the workspace");
 
-  // Once per device, with that device current: the device address of this
-  // device's copy of the array.  Host code may not use the array's name as an
-  // address; only the address returned here is valid for kernels.
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MMS_ERR_CUDA;
+  // Host code may not use the array's name as an address; only the address
+  // looked up here is valid for kernels.
   void* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || p == nullptr) return MMS_ERR_CUDA;
-      g_scratch_ptr[dev] = p;
-    }
-    scratch = g_scratch_ptr[dev];
-  }
-  // The array keeps the previous call's contents: its status word must start
-  // at zero.  The rest (ping-pong keys, pivot table) is fully overwritten.
-  if (cudaMemsetAsync(scratch, 0, 256, (cudaStream_t)stream) != cudaSuccess) return MMS_ERR_CUDA;
+  const mms_status st = scratch_address(&scratch);
+  if (st != MMS_OK) return st;
+  // The array keeps the previous call's contents; mms_sort_keys_ex clears the
+  // status word of a caller's workspace first, and the rest (ping-pong keys,
+  // pivot table) is fully overwritten.
   return mms_sort_keys_ex(kt, d_keys, n, scratch, kNoAllocScratchBytes, stream, nullptr);
+}
+
+extern "C" mms_status mms_noalloc_status(void* stream) {
+  void* scratch = nullptr;
+  const mms_status st = scratch_address(&scratch);
+  if (st != MMS_OK) return st;
+  return mms_workspace_status(scratch, kNoAllocScratchBytes, stream);
 }

@@ -16,7 +16,10 @@ __global__ void __launch_bounds__(256)
     pairs_finalize_kernel(const uint64_t* __restrict__ comp, const uint32_t* __restrict__ vals_src,
                           uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                           long long n) {
-  const long long nq = n / 4;
+  // 16-byte stores where both outputs lie on the 16-byte grid (keys and values
+  // may start at any 4-byte offset), one item at a time otherwise.
+  const bool vec = (((uintptr_t)keys_out | (uintptr_t)vals_out) & 15u) == 0;
+  const long long nq = vec ? n / 4 : 0;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
     const ulonglong2 a = reinterpret_cast<const ulonglong2*>(comp)[2 * q];

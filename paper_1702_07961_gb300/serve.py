@@ -95,6 +95,7 @@ class Request:
     start: float | None = None
     finish: float | None = None
     group: int = -1
+    error: str | None = None                  # set when the group's sort reported a device error
 
     @property
     def n(self) -> int:
@@ -143,6 +144,22 @@ def form_group(queue, small_max: int, batch_max: int, max_segments: int):
     return group
 
 
+# Workspace status words the library writes (the first word of a workspace).
+_DEVICE_ERRORS = {1: "device-side wait timed out", 2: "device consistency check failed"}
+
+
+def finish_group(reqs, status_word: int, t: float) -> None:
+    """Marks a completed launch group's requests finished at time t; a non-zero
+    workspace status word means the sort stopped early on the device, so its
+    results are not sorted: every request of the group is marked failed."""
+    err = None
+    if status_word != 0:
+        err = _DEVICE_ERRORS.get(int(status_word), f"device status {int(status_word)}")
+    for r in reqs:
+        r.finish = t
+        r.error = err
+
+
 @dataclass
 class _Launch:
     reqs: list
@@ -151,6 +168,7 @@ class _Launch:
     event: object
     slot: int
     keep: list = field(default_factory=list)
+    status: object = None                     # pinned copy of the workspace status word
 
 
 class SortServer:
@@ -253,9 +271,14 @@ class SortServer:
                 if pairs:
                     r.out_values.copy_(vals[pos:pos + r.n], non_blocking=True)
                 pos += r.n
+            # The sort cleared its workspace's status word before running; read
+            # it back with the results, so a sort stopped on the device is
+            # reported as failed rather than returned as sorted.
+            status = torch.empty(1, dtype=torch.int32, pin_memory=True)
+            status.copy_(ws[:4].view(torch.int32), non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        self.inflight.append(_Launch(reqs, off, st, ev, slot, keep))
+        self.inflight.append(_Launch(reqs, off, st, ev, slot, keep, status))
         self.max_inflight = max(self.max_inflight, len(self.inflight))
         self.groups += 1
         return True
@@ -265,9 +288,7 @@ class SortServer:
         still = []
         for g in self.inflight:
             if g.event.query():
-                t = clock()
-                for r in g.reqs:
-                    r.finish = t
+                finish_group(g.reqs, int(g.status[0]) if g.status is not None else 0, clock())
                 self.arena.free(g.offset)
                 self.free_slots.append(g.slot)
                 done += len(g.reqs)
@@ -368,6 +389,7 @@ def summarize(reqs) -> dict:
     lat = np.array([r.latency() for r in reqs]) * 1e3
     keys = sum(r.n for r in reqs)
     span = max(r.finish for r in reqs) - min(r.arrival for r in reqs)
-    return {"requests": len(reqs), "keys": keys, "seconds": span, "gkeys_per_s": keys / span / 1e9,
+    return {"requests": len(reqs), "failed": sum(r.error is not None for r in reqs),
+            "keys": keys, "seconds": span, "gkeys_per_s": keys / span / 1e9,
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
             "latency_ms_mean": float(lat.mean())}

@@ -72,9 +72,12 @@ def test_workspace_grows_with_n(lib):
 
 
 def test_argument_checks_need_no_gpu(lib):
-    # null keys, misaligned keys, bad fanout: rejected before any CUDA call
+    # null keys, keys not aligned to the key size, bad fanout: rejected before any CUDA call
     assert lib.mms_sort_keys(0, None, 100, None, 0, None) == 1
-    assert lib.mms_sort_keys(0, ctypes.c_void_p(4), 100, None, 0, None) == 1
+    assert lib.mms_sort_keys(0, ctypes.c_void_p(2), 100, None, 0, None) == 1       # u32 at 2 bytes
+    assert lib.mms_sort_keys(1, ctypes.c_void_p(4), 100, None, 0, None) == 1       # u64 at 4 bytes
+    assert lib.mms_sort_pairs(0, ctypes.c_void_p(256), ctypes.c_void_p(6), 100, None, 0, None) == 1
+    assert lib.mms_tile_sort(2, ctypes.c_void_p(258), ctypes.c_void_p(256), 100, None) == 1
     assert lib.mms_sort_keys(7, ctypes.c_void_p(256), 100, None, 0, None) == 1
     assert lib.mms_sort_keys(0, None, 1, None, 0, None) == 0       # n <= 1 is a no-op
     assert lib.mms_splitter(2, ctypes.c_void_p(256), 100, 8192, 4, ctypes.c_void_p(256), None) == 2

@@ -56,6 +56,7 @@ def test_served_mix_equals_oracle_and_alone(gpu):
     srv.run(reqs)
     assert srv.coalesced > 0 and srv.groups < len(reqs), "no request was coalesced"
     assert srv.max_inflight > 1, "launch groups never overlapped"
+    assert all(r.error is None for r in reqs), "a launch group reported a device-side error"
     alone = serve_serial(clone(reqs))
     for r, a in zip(sorted(reqs, key=lambda x: x.rid), sorted(alone, key=lambda x: x.rid)):
         gk, gv = outputs(r)

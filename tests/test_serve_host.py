@@ -4,7 +4,8 @@ import numpy as np
 import pytest
 
 from paper_1702_07961_gb300 import KEY_F32, KEY_U32, KEY_U64
-from paper_1702_07961_gb300.serve import DeviceArena, Request, form_group, poisson_arrivals
+from paper_1702_07961_gb300.serve import (DeviceArena, Request, finish_group, form_group,
+                                          poisson_arrivals, summarize)
 
 
 def test_arena_first_fit_and_merge():
@@ -92,3 +93,18 @@ def test_plan_cost_fit_skips_partial_last_rounds():
     assert got["u32"][0] == pytest.approx((1.1 + 1.1 + 0.6) / 3)
     for c in got["u32"][1:] + got["u64"][1:]:
         assert c == pytest.approx(1.1)
+
+
+def test_nonzero_status_word_marks_the_group_failed():
+    """A sort stopped on the device (workspace status word non-zero) must not be
+    returned as a sorted result: every request of its launch group fails."""
+    ok = [req(0, 10), req(1, 20)]
+    finish_group(ok, 0, 1.5)
+    assert all(r.finish == 1.5 and r.error is None for r in ok)
+    timed_out = [req(2, 10), req(3, 30)]
+    finish_group(timed_out, 1, 2.0)                 # the device's time-out word
+    assert all(r.finish == 2.0 and "timed out" in r.error for r in timed_out)
+    bad = [req(4, 10)]
+    finish_group(bad, 2, 2.5)                       # a failed consistency check
+    assert "consistency" in bad[0].error
+    assert summarize(ok + timed_out + bad)["failed"] == 3

@@ -47,6 +47,7 @@ def test_noalloc_matches_sort_keys_on_two_calls(gpu, dtype):
         got = _dev(keys)
         status = L.mms_sort_keys_noalloc(kt, ctypes.c_void_p(got.data_ptr()), n, stream)
         assert status == 0
+        assert L.mms_noalloc_status(stream) == 0        # no device-side error recorded
         assert np.array_equal(_bits(got, dtype), _bits(ref, dtype)), f"call {call}: outputs differ"
 
 
