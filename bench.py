@@ -45,6 +45,16 @@ def parse():
     p.add_argument("--fanout", type=int, default=0, help="merge fanout K (0 = planner)")
     p.add_argument("--tile", type=int, default=0, help="tile items (0 = library default)")
     p.add_argument("--pairs", action="store_true", help="key + uint32 index payload (stable key-value sort)")
+    p.add_argument("--key", default="u32", choices=["u32", "u64", "f32"],
+                   help="sort workload: key type (the headline is u32)")
+    p.add_argument("--input", default="permutation", choices=["permutation", "sortedness", "interleaved"],
+                   help="sort workload: a uniform permutation (the headline), a sortedness input with "
+                        "--swaps pair swaps, or --runs runs interleaved at --stride")
+    p.add_argument("--swaps", type=int, default=0)
+    p.add_argument("--runs", type=int, default=8)
+    p.add_argument("--stride", type=int, default=32)
+    p.add_argument("--min-timed-s", type=float, default=1.0,
+                   help="repeat the K-step timed window until the windows span this many seconds")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-slots", type=int, default=3,
                    help="end-to-end pipeline depth: steps in flight, each with its own buffers and stream")
@@ -142,14 +152,25 @@ def gpu_uuid(dev: int) -> str:
 # ---- CPU oracle timing --------------------------------------------------------------
 
 def time_oracle(keys_np, sample: int):
+    """The oracle on the host: the textbook stable mergesort with its top
+    recursion levels on every core (the record reported), and the plain
+    single-threaded run beside it."""
     import oracle
+    cores = oracle.host_cores()
     s = keys_np[:sample].copy()
     t0 = time.perf_counter()
-    oracle.sort(s)
-    dt = time.perf_counter() - t0
-    return {"value": s.shape[0] / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {s.shape[0]} keys of the workload, single-threaded textbook stable mergesort",
-            "seconds": round(dt, 3)}
+    oracle.sort_parallel(s, None, cores)
+    dt_all = time.perf_counter() - t0
+    s1 = keys_np[:sample].copy()
+    t0 = time.perf_counter()
+    oracle.sort(s1)
+    dt_one = time.perf_counter() - t0
+    return {"value": s.shape[0] / dt_all / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {s.shape[0]} keys of the workload; textbook stable top-down mergesort, "
+                      f"top recursion levels split over {cores} host threads",
+            "seconds": round(dt_all, 3),
+            "single_core": {"value": s1.shape[0] / dt_one / 1e9, "unit": UNIT, "cores": 1,
+                            "seconds": round(dt_one, 3)}}
 
 
 def run_reference(args):
@@ -158,16 +179,17 @@ def run_reference(args):
         return 0
     import numpy as np
     import synth
-    n_sample = min(args.n, 1 << 22)
-    keys = synth.permutation(args.n, 1)[:n_sample].copy()      # first keys of the GPU arm's workload
     import oracle
+    cores = oracle.host_cores()
+    n_sample = min(args.n, 1 << 23)
+    keys = synth.permutation(args.n, 1)[:n_sample].copy()      # first keys of the GPU arm's workload
     for _ in range(args.warmup):
-        oracle.sort(keys)
+        oracle.sort_parallel(keys, None, cores)
     times = []
     for _ in range(args.steps):
         s = keys.copy()
         t0 = time.perf_counter()
-        oracle.sort(s)
+        oracle.sort_parallel(s, None, cores)
         times.append(time.perf_counter() - t0)
     sec = sum(times)
     value = n_sample * args.steps / sec / 1e9
@@ -179,8 +201,9 @@ def run_reference(args):
         "config": {"workload": f"uniform random permutation of 0..N-1, N={args.n} uint32 (Sec. 6.3 fully random); "
                                f"reference arm sorts a {n_sample}-key sample per step on the host",
                    "global_batch": n_sample, "seq_len": None, "parallelism": "cpu"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{n_sample} keys of the workload per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n_sample} keys of the workload per step, textbook stable mergesort "
+                                   f"with its top recursion levels on {cores} host threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -201,25 +224,107 @@ def aggregate_over_ranks(total_ms: float, keys_per_rank: int, steps: int, world:
     return ms, keys_per_rank * world / (ms / 1e3) / 1e9
 
 
-def kernel_source_hash() -> str:
+def hbm_peak() -> float:
+    """Measured HBM copy bandwidth of the GB300s (GB/s), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
+KERNEL_SOURCES = {
+    "merge_pass_kernel": ["merge_pass.cu", "merge_tile.cuh", "mms_common.cuh", "mms_kernels.cuh"],
+    "tile_sort_kernel": ["tile_sort.cu", "tile_sort.cuh", "mms_common.cuh", "mms_kernels.cuh"],
+}
+
+
+def kernel_source_hash(kernel: str = "merge_pass_kernel") -> str:
     h = hashlib.sha256()
-    for f in ["merge_pass.cu", "merge_tile.cuh", "mms_common.cuh", "mms_kernels.cuh"]:
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1702_07961_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def load_traffic(n: int):
-    """DRAM bytes per merge-pass launch from the committed ncu summary, scaled to
-    this workload; None when absent or taken on a different kernel source."""
+def load_traffic(n: int, kernel: str):
+    """DRAM bytes (read + write) of one launch of `kernel` from the committed ncu
+    summary, taken at the bench workload's size (scaled if n differs, the
+    traffic being proportional to the keys moved); None when absent or taken
+    on a different kernel source."""
     try:
         with open(PROFILE_TRAFFIC) as f:
-            p = json.load(f)
-    except (OSError, ValueError):
+            p = json.load(f).get(kernel)
+    except (OSError, ValueError, AttributeError):
         return None
-    if p.get("kernel_source_hash") != kernel_source_hash():
+    if not p or p.get("kernel_source_hash") != kernel_source_hash(kernel):
         return None
-    return p["dram_bytes_per_key"] * n
+    return p["dram_bytes_per_launch"] * n / p["n"]
+
+
+def make_sort_input(args, N: int, rank: int):
+    """The sort workload's keys (numpy, host) and a description: a uniform
+    permutation of 0..N-1 (Sec. 6.3 'fully random', the headline), a
+    sortedness input (Sec. 1), runs interleaved at a stride (the C3 layout),
+    or N(0,1) floats with duplicates, -0.0 and NaNs for f32 keys."""
+    import numpy as np
+    import synth
+    if args.key == "f32":
+        return synth.normal_f32(N, 3 + rank), "N(0,1) float32 with 1% duplicates, 0.1% -0.0, 0.01% NaN"
+    if args.input == "sortedness":
+        v = synth.sortedness_cached(N, args.swaps, 2 + rank) if args.swaps >= 10**6 else \
+            synth.sortedness(N, args.swaps, 2 + rank)
+        desc = f"sortedness: 0..N-1 then {args.swaps} random pair swaps (Sec. 1)"
+    elif args.input == "interleaved":
+        v = synth.interleaved(N, args.runs, args.stride)
+        desc = f"{args.runs} sorted runs interleaved at stride {args.stride} (C3 layout)"
+    else:
+        v = synth.permutation(N, 1 + rank)
+        desc = "uniform random permutation of 0..N-1 (Sec. 6.3 'fully random')"
+    if args.key == "u64":
+        w = v.astype(np.uint64)
+        return (w << np.uint64(32)) | w, desc + ", as u64 keys (v << 32 | v)"
+    return v.astype(np.uint32), desc
+
+
+def verify_sort(work, src, vals, args, N: int) -> bool:
+    """Checks one sort of the workload on the device.  Integer inputs whose
+    values are 0..N-1 (permutation, sortedness, interleaved at a multiple of
+    runs x stride) must sort to iota (v << 32 | v for u64), with the index
+    payload becoming the inverse permutation; otherwise the output must be
+    non-decreasing (totalOrder for floats) with an unchanged multiset hash."""
+    import torch
+    dev = work.device
+    dense = args.input != "interleaved" or N % (args.runs * args.stride) == 0
+    if args.key != "f32" and dense:
+        iota = torch.arange(N, dtype=torch.int64, device=dev)
+        if args.key == "u64":
+            ok = bool(torch.equal(work, (iota << 32) | iota))
+            kv = work & 0xFFFFFFFF
+        else:
+            ok = bool(torch.equal(work.to(torch.int64) & 0xFFFFFFFF, iota))
+            kv = src.to(torch.int64) & 0xFFFFFFFF
+        if vals is not None and ok:
+            if args.key == "u64":
+                kv = src & 0xFFFFFFFF
+            inv = torch.empty(N, dtype=torch.int64, device=dev)
+            inv[kv] = iota
+            ok = bool(torch.equal(vals.to(torch.int64) & 0xFFFFFFFF, inv))
+        return ok
+    if args.key == "f32":
+        b = work.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+        sb = src.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+        ordv = torch.where(b >= 2**31, 0xFFFFFFFF - b, b + 2**31)     # totalOrder on bit patterns
+        ok = bool(torch.all(ordv[1:] >= ordv[:-1]))
+    elif args.key == "u64":
+        b, sb = work, src
+        hi, lo = (work >> 32) & 0xFFFFFFFF, work & 0xFFFFFFFF
+        ok = bool(torch.all((hi[1:] > hi[:-1]) | ((hi[1:] == hi[:-1]) & (lo[1:] >= lo[:-1]))))
+    else:
+        b, sb = work.to(torch.int64) & 0xFFFFFFFF, src.to(torch.int64) & 0xFFFFFFFF
+        ok = bool(torch.all(b[1:] >= b[:-1]))
+    mix = lambda x: ((x * 0x9E3779B97F4A7C15) ^ (x >> 7)) & 0xFFFFFFFFFFFF
+    return ok and bool(mix(b).sum() == mix(sb).sum())
 
 
 TUNED = os.path.join(ROOT, "paper_1702_07961_gb300", "tuned", "batched_u32_pairs.json")
@@ -536,7 +641,7 @@ def run_configs(args):
         kb = 8 if (pairs or kt == mms.KEY_U64) else 4
         results.append({"config": name, "n": n, "ms": ms, "gkeys_per_s": n / ms / 1e6, "verified": bool(ok),
                         "fanouts": plan, "passes": passes,
-                        "hbm_frac_whole_sort": passes * 2 * n * kb / (ms / 1e3) / 1e9 / 6787.6, "note": note})
+                        "hbm_frac_whole_sort": passes * 2 * n * kb / (ms / 1e3) / 1e9 / hbm_peak(), "note": note})
 
     # C1: 2^20 uniform u32, bit-exact against the oracle
     n = 1 << 20
@@ -667,7 +772,7 @@ def run_sweep(args):
                 rows.append({"key": name, "n": n, "K": K, "rounds": len(plan), "ms": tot,
                              "gkeys_per_s": n / tot / 1e6, "tile_sort_ms": statistics.mean(x[0] for x in st),
                              "merge_pass_ms_avg": statistics.mean(merge) if merge else None,
-                             "merge_pass_hbm_frac": (2 * n * kb / (statistics.mean(merge) / 1e3) / 1e9 / 6787.6)
+                             "merge_pass_hbm_frac": (2 * n * kb / (statistics.mean(merge) / 1e3) / 1e9 / hbm_peak())
                              if merge else None,
                              "splitters_ms": split, "merge_pass_ms": merge, "splitter_ms": split_r,
                              "runs_merged": merged, "verified": ok})
@@ -706,13 +811,16 @@ def main():
 
     dev = torch.device("cuda", local)
     N = args.n
-    keys_np = synth.permutation(N, 1 + rank)
-    src = torch.from_numpy(keys_np.view(np.int32)).to(dev)
+    kt = {"u32": mms.KEY_U32, "u64": mms.KEY_U64, "f32": mms.KEY_F32}[args.key]
+    kb = 8 if args.key == "u64" else 4
+    keys_np, input_desc = make_sort_input(args, N, rank)
+    host_view = keys_np.view(np.int64 if kb == 8 else (np.float32 if args.key == "f32" else np.int32))
+    src = torch.from_numpy(host_view).to(dev)
     work = torch.empty_like(src)
-    vals = torch.empty_like(src)
+    vals = torch.empty(N, dtype=torch.int32, device=dev)
     iota32 = torch.arange(N, dtype=torch.int32, device=dev)
-    ws = torch.zeros(mms.workspace_bytes(mms.KEY_U32, N, args.pairs), dtype=torch.uint8, device=dev)
-    plan = mms.plan(mms.KEY_U32, N, args.fanout, args.tile, pairs=args.pairs)
+    ws = torch.zeros(mms.workspace_bytes(kt, N, args.pairs), dtype=torch.uint8, device=dev)
+    plan = mms.plan(kt, N, args.fanout, args.tile, pairs=args.pairs)
     n_ev = 2 + 2 * len(plan) + (1 if args.pairs else 0)
     stream = torch.cuda.current_stream()
 
@@ -720,57 +828,64 @@ def main():
         work.copy_(src)
         if args.pairs:
             vals.copy_(iota32)
-            mms.sort_pairs(work, vals, fanout=args.fanout, workspace=ws, kt=mms.KEY_U32, events=events,
+            mms.sort_pairs(work, vals, fanout=args.fanout, workspace=ws, kt=kt, events=events,
                            tile_items=args.tile)
         else:
-            mms.sort_keys(work, fanout=args.fanout, workspace=ws, kt=mms.KEY_U32, events=events,
+            mms.sort_keys(work, fanout=args.fanout, workspace=ws, kt=kt, events=events,
                           tile_items=args.tile)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    iota = torch.arange(N, dtype=torch.int64, device=dev)
-    verified = bool(torch.equal(work.to(torch.int64) & 0xFFFFFFFF, iota))
-    if args.pairs:
-        inv = torch.empty(N, dtype=torch.int64, device=dev)
-        inv[src.to(torch.int64) & 0xFFFFFFFF] = iota
-        verified = verified and bool(torch.equal(vals.to(torch.int64), inv))
-        del inv
-    del iota
+    verified = verify_sort(work, src, vals if args.pairs else None, args, N)
     mms.workspace_status(ws)
     if not verified:
         raise SystemExit("bench: sorted output is wrong")
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
+    # Timed windows of exactly K steps each (barrier + synchronize on both
+    # sides, max over ranks), repeated until they span --min-timed-s seconds so
+    # that the clock record and the median rest on more than a few ms.
     sampler = ClockSampler(gpu_uuid(local))
     sampler.start()
     time.sleep(0.5)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
+    windows = []
+    stage = []
     t0 = time.time()
-    for s in range(args.steps):
-        step(evs[s])
-    torch.cuda.synchronize()
+    while True:
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for s_ in range(args.steps):
+            step(evs[s_])
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        step_ms = [e[0].elapsed_time(e[-1]) for e in evs]
+        stage += [[e[i].elapsed_time(e[i + 1]) for i in range(n_ev - 1)] for e in evs]
+        windows.append(aggregate_over_ranks(sum(step_ms), N, args.steps, world, dev))
+        spent = sum(w[0] for w in windows) * args.steps / 1e3
+        # every rank takes the same decision: the window times are max-reduced
+        if spent >= args.min_timed_s or len(windows) >= 200:
+            break
     t1 = time.time()
-    if world > 1:
-        torch.distributed.barrier()
     sampler.stop()
     mms.workspace_status(ws)
+    if not verify_sort(work, src, vals if args.pairs else None, args, N):
+        raise SystemExit("bench: sorted output is wrong after the timed windows")
+    order = sorted(range(len(windows)), key=lambda i: windows[i][0])
+    ms_per_step, value = windows[order[len(order) // 2]]          # the median window
 
-    step_ms = [e[0].elapsed_time(e[-1]) for e in evs]
-    stage = [[e[i].elapsed_time(e[i + 1]) for i in range(n_ev - 1)] for e in evs]
-    ms_per_step, value = aggregate_over_ranks(sum(step_ms), N, args.steps, world, dev)
-
-    # per-kernel averages over the timed steps: [tile_sort, (splitter, merge) per round,
+    # per-kernel averages over every timed step: [tile_sort, (splitter, merge) per round,
     # (value gather for pairs)]
-    avg = [statistics.mean(s[i] for s in stage) for i in range(n_ev - 1)]
+    avg = [statistics.mean(s_[i] for s_ in stage) for i in range(n_ev - 1)]
     tile_ms = avg[0]
     split_ms = [avg[1 + 2 * r] for r in range(len(plan))]
     merge_ms = [avg[2 + 2 * r] for r in range(len(plan))]
     gather_ms = avg[-1] if args.pairs else None
     # algorithmic bytes of one pass: every key (8-byte composite for pairs) read and written once
-    bytes_pass = 2 * N * (8 if args.pairs else KEY_BYTES)
+    item_bytes = 8 if args.pairs else kb
+    bytes_pass = 2 * N * item_bytes
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -789,28 +904,41 @@ def main():
         achieved = bytes_pass / (merge_avg / 1e3) / 1e9
     else:
         achieved = bytes_pass / (tile_ms / 1e3) / 1e9
-    traffic = load_traffic(N)
+    headline = args.key == "u32" and not args.pairs and args.input == "permutation"
+    traffic = load_traffic(N, "merge_pass_kernel") if headline and merge_avg else None
     roofline = {"bound": "hbm", "kernel": "merge_pass" if merge_avg else "tile_sort",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_src, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one merge_pass_kernel "
+                                  "launch at this workload (profiles/merge_pass_traffic.json)" if traffic else None,
                 "algorithmic_bytes_per_launch": bytes_pass,
                 "per_pass_frac": [bytes_pass / (m / 1e3) / 1e9 / peak for m in merge_ms],
                 "tile_sort_frac": bytes_pass / (tile_ms / 1e3) / 1e9 / peak}
+    if headline:
+        roofline["tile_sort_traffic"] = load_traffic(N, "tile_sort_kernel")
 
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if headline else f"Gkeys/s at {N} {args.key}" + (" pairs" if args.pairs else ""),
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"uniform random permutation of 0..N-1, N={N} uint32 keys, "
+        "vs_baseline": None, "dtype": args.key, "data": "synthetic",
+        "config": {"workload": f"{input_desc}, N={N} {args.key} keys, "
                                + ("key + uint32 index payload (stable)" if args.pairs else "key-only")
-                               + " (Sec. 6.3 'fully random'), one sort per step",
+                               + ", one sort per step",
                    "global_batch": N * world, "seq_len": None, "parallelism": f"replicas{world}",
-                   "plan_fanouts": plan, "tile": args.tile or mms.tile_items(mms.KEY_U32),
-                   "l2": "input 400 MB > 129 MB L2; a 400 MB copy restores the input between steps"},
+                   "plan_fanouts": plan, "tile": args.tile or mms.tile_items(kt),
+                   "l2": f"input {N * kb / 1e6:.0f} MB > 129 MB L2; a device copy restores the input "
+                         "before every step, outside the timed events" if N * kb > 129e6 else
+                         "input fits in L2"},
+        "timed_windows": {"count": len(windows), "steps_each": args.steps,
+                          "gkeys_per_s": [w[1] for w in windows],
+                          "note": "value and ms_per_step are the median window's"},
         "stages_ms": {"tile_sort": tile_ms, "splitter": split_ms, "merge_pass": merge_ms,
                       "pairs_finalize": gather_ms, "dominant": dominant},
         "roofline": roofline,
-        "gpu_launches": args.steps * (1 + 2 * len(plan) + (1 if args.pairs else 0)),
+        "gpu_launches": len(windows) * args.steps * (1 + 2 * len(plan) + (1 if args.pairs else 0)),
+        "gpu_launches_note": "kernels of the timed windows: base case, splitter and merge pass per round"
+                             + (", value gather" if args.pairs else ""),
         "verified_vs_closed_form": verified,
         "clocks": sampler.summary(t0, t1),
     }
@@ -819,26 +947,26 @@ def main():
     # ceil(log2 K) on-chip tree levels per HBM read and write.  Measure the
     # merge pass alone at K = 2 and K = 4 too (same workload, same timing).
     by_k = {}
-    if not args.pairs:
+    if headline:
         for kf in (2, 4):
-            planf = mms.plan(mms.KEY_U32, N, kf, args.tile)
+            planf = mms.plan(kt, N, kf, args.tile)
             nf = 2 + 2 * len(planf)
             evf = [[torch.cuda.Event(enable_timing=True) for _ in range(nf)] for _ in range(10)]
             for i in range(13):
                 work.copy_(src)
-                mms.sort_keys(work, fanout=kf, workspace=ws, kt=mms.KEY_U32, tile_items=args.tile,
+                mms.sort_keys(work, fanout=kf, workspace=ws, kt=kt, tile_items=args.tile,
                               events=evf[i - 3] if i >= 3 else None)
             torch.cuda.synchronize()
             # merge pass of round r: from event 2 + 2r (after its splitter) to 3 + 2r
             mf = statistics.mean(statistics.mean(e[2 + 2 * r].elapsed_time(e[3 + 2 * r])
                                                  for r in range(len(planf)))
                                  for e in evf)
-            okf = bool(torch.equal(work.to(torch.int64) & 0xFFFFFFFF, torch.arange(N, dtype=torch.int64, device=dev)))
+            okf = verify_sort(work, src, None, args, N)
             by_k[str(kf)] = {"merge_pass_ms": mf, "frac": bytes_pass / (mf / 1e3) / 1e9 / peak,
                              "sort_ms": statistics.mean(e[0].elapsed_time(e[-1]) for e in evf), "verified": okf}
         roofline["per_pass_frac_by_fanout"] = by_k
 
-    if not args.no_e2e and not args.pairs:
+    if not args.no_e2e and headline:
         # End to end through the public API: every step copies its input from
         # pinned host memory, sorts it (mms_sort_keys) and copies the result
         # back to pinned host memory.  --e2e-slots slots (device buffer,
@@ -894,7 +1022,8 @@ def main():
         ok = ok and bool(np.array_equal(sl["out"].numpy().view(np.uint32), iota_np))
         out["e2e"] = {"value": N / (pipe_ms / 1e3) / 1e9 * world, "unit": UNIT,
                       "h2d_bytes_per_step": N * KEY_BYTES, "d2h_bytes_per_step": N * KEY_BYTES,
-                      "ms_per_step": pipe_ms, "steps": n_e2e, "verified_all_outputs": ok,
+                      "ms_per_step": pipe_ms, "steps": n_e2e,
+                      "verified_last_output_of_every_slot": ok,
                       "mode": f"{ns} slots taking the steps in turn: uploads and downloads overlap other "
                               "steps' sorts",
                       "one_at_a_time": {"value": N / (ser_ms / 1e3) / 1e9 * world, "ms_per_step": ser_ms}}

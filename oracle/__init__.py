@@ -55,7 +55,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD_DIR, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-pthread", "-fPIC", "-shared", "-o", tmp, _SRC])
         os.replace(tmp, _SO)
     return _SO
 
@@ -68,6 +68,9 @@ def lib() -> ctypes.CDLL:
             L = ctypes.CDLL(so)
             L.oracle_sort.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
             L.oracle_sort.restype = ctypes.c_int
+            L.oracle_sort_threads.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_size_t, ctypes.c_int]
+            L.oracle_sort_threads.restype = ctypes.c_int
             L.oracle_argsort.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
             L.oracle_argsort.restype = ctypes.c_int
             L.oracle_less.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t]
@@ -126,6 +129,32 @@ def sort(keys: np.ndarray, values: np.ndarray | None = None):
     if rc != 0:
         raise MemoryError(f"oracle_sort failed ({rc})")
     return k, v
+
+
+def sort_parallel(keys: np.ndarray, values: np.ndarray | None = None, threads: int | None = None):
+    """:func:`sort` with the mergesort's top recursion levels split over
+    ``threads`` host threads (default: every core this process may use).  The
+    same ranges are split and merged the same way, so the result is the
+    same; only the CPU baseline's timing uses it."""
+    if threads is None:
+        threads = host_cores()
+    k = np.array(keys, copy=True, order="C")
+    v = None if values is None else np.array(values, dtype=np.uint32, copy=True, order="C")
+    if v is not None and v.shape[0] != k.shape[0]:
+        raise ValueError("keys and values differ in length")
+    rc = lib().oracle_sort_threads(KEY_TYPES[key_type_of(k)], k.ctypes.data,
+                                   None if v is None else v.ctypes.data, k.shape[0], int(threads))
+    if rc != 0:
+        raise MemoryError(f"oracle_sort_threads failed ({rc})")
+    return k, v
+
+
+def host_cores() -> int:
+    """Cores this process may run on (the affinity mask, else the CPU count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
 def tile_sort(keys: np.ndarray, tile: int, values: np.ndarray | None = None):

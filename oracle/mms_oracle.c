@@ -25,6 +25,8 @@
  * that the test suite can show its pins catch it.  Mutation 0 (the default)
  * is the correct oracle.
  */
+#define _POSIX_C_SOURCE 200809L
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -87,13 +89,10 @@ int oracle_less(int key_type, const void* keys, size_t i, size_t j) {
 
 /* ---- stable top-down two-way mergesort on an index permutation --------- */
 
-static void merge_sort_rec(int kt, const void* keys, uint64_t* idx,
-                           uint64_t* tmp, size_t lo, size_t hi) {
-  size_t mid, i, j, o;
-  if (hi - lo < 2) return;
-  mid = lo + (hi - lo) / 2;
-  merge_sort_rec(kt, keys, idx, tmp, lo, mid);
-  merge_sort_rec(kt, keys, idx, tmp, mid, hi);
+/* Merges the sorted halves idx[lo, mid) and idx[mid, hi) through tmp. */
+static void merge_halves(int kt, const void* keys, uint64_t* idx, uint64_t* tmp,
+                         size_t lo, size_t mid, size_t hi) {
+  size_t i, j, o;
   i = lo;
   j = mid;
   o = lo;
@@ -112,6 +111,61 @@ static void merge_sort_rec(int kt, const void* keys, uint64_t* idx,
   memcpy(idx + lo, tmp + lo, (hi - lo) * sizeof(uint64_t));
 }
 
+static void merge_sort_rec(int kt, const void* keys, uint64_t* idx,
+                           uint64_t* tmp, size_t lo, size_t hi) {
+  size_t mid;
+  if (hi - lo < 2) return;
+  mid = lo + (hi - lo) / 2;
+  merge_sort_rec(kt, keys, idx, tmp, lo, mid);
+  merge_sort_rec(kt, keys, idx, tmp, mid, hi);
+  merge_halves(kt, keys, idx, tmp, lo, mid, hi);
+}
+
+/* The same recursion with its top `depth` levels run as threads: the left
+ * half of every such level on a new thread, the right half on this one, then
+ * the same merge.  It splits the same ranges and merges them the same way, so
+ * its result equals merge_sort_rec's; only the CPU baseline's timing uses it. */
+typedef struct {
+  int kt;
+  const void* keys;
+  uint64_t* idx;
+  uint64_t* tmp;
+  size_t lo, hi;
+  int depth;
+} sort_task;
+
+static void* merge_sort_task(void* arg);
+
+static void merge_sort_par(const sort_task* t) {
+  size_t mid;
+  pthread_t th;
+  sort_task left, right;
+  if (t->depth <= 0 || t->hi - t->lo < ((size_t)1 << 16)) {
+    merge_sort_rec(t->kt, t->keys, t->idx, t->tmp, t->lo, t->hi);
+    return;
+  }
+  mid = t->lo + (t->hi - t->lo) / 2;
+  left = *t;
+  left.hi = mid;
+  left.depth = t->depth - 1;
+  right = *t;
+  right.lo = mid;
+  right.depth = t->depth - 1;
+  if (pthread_create(&th, NULL, merge_sort_task, &left) != 0) {
+    merge_sort_par(&left);                  /* no thread to spare: same work, in order */
+    merge_sort_par(&right);
+  } else {
+    merge_sort_par(&right);
+    pthread_join(th, NULL);
+  }
+  merge_halves(t->kt, t->keys, t->idx, t->tmp, t->lo, mid, t->hi);
+}
+
+static void* merge_sort_task(void* arg) {
+  merge_sort_par((const sort_task*)arg);
+  return NULL;
+}
+
 /* perm[p] = input index of the item that lands at output position p. */
 int oracle_argsort(int key_type, const void* keys, size_t n, uint64_t* perm) {
   uint64_t* tmp;
@@ -126,10 +180,36 @@ int oracle_argsort(int key_type, const void* keys, size_t n, uint64_t* perm) {
   return 0;
 }
 
+/* oracle_argsort with the recursion's top levels on up to `threads` threads. */
+int oracle_argsort_parallel(int key_type, const void* keys, size_t n, uint64_t* perm,
+                            int threads) {
+  uint64_t* tmp;
+  size_t i;
+  sort_task t;
+  int depth = 0;
+  if (key_type < KEY_U32 || key_type > KEY_F32) return -2;
+  for (i = 0; i < n; ++i) perm[i] = i;
+  if (n < 2) return 0;
+  tmp = (uint64_t*)malloc(n * sizeof(uint64_t));
+  if (!tmp) return -1;
+  while ((1 << depth) < threads && depth < 10) ++depth;
+  t.kt = key_type;
+  t.keys = keys;
+  t.idx = perm;
+  t.tmp = tmp;
+  t.lo = 0;
+  t.hi = n;
+  t.depth = depth;
+  merge_sort_par(&t);
+  free(tmp);
+  return 0;
+}
+
 static size_t key_bytes(int key_type) { return key_type == KEY_U64 ? 8 : 4; }
 
-/* Sorts keys (and values, when not NULL) in place, stably. */
-int oracle_sort(int key_type, void* keys, uint32_t* values, size_t n) {
+/* Sorts keys (and values, when not NULL) in place, stably; threads > 1 runs
+ * the recursion's top levels in parallel (same result). */
+int oracle_sort_threads(int key_type, void* keys, uint32_t* values, size_t n, int threads) {
   uint64_t* perm;
   unsigned char* kcopy;
   uint32_t* vcopy = NULL;
@@ -146,7 +226,8 @@ int oracle_sort(int key_type, void* keys, uint32_t* values, size_t n) {
     free(vcopy);
     return -1;
   }
-  rc = oracle_argsort(key_type, keys, n, perm);
+  rc = threads > 1 ? oracle_argsort_parallel(key_type, keys, n, perm, threads)
+                   : oracle_argsort(key_type, keys, n, perm);
   if (rc == 0) {
     memcpy(kcopy, keys, n * kb);
     if (values) memcpy(vcopy, values, n * sizeof(uint32_t));
@@ -159,4 +240,9 @@ int oracle_sort(int key_type, void* keys, uint32_t* values, size_t n) {
   free(kcopy);
   free(vcopy);
   return rc;
+}
+
+/* Sorts keys (and values, when not NULL) in place, stably. */
+int oracle_sort(int key_type, void* keys, uint32_t* values, size_t n) {
+  return oracle_sort_threads(key_type, keys, values, n, 1);
 }

@@ -21,9 +21,15 @@ Workload shapes (Sec. 1 and Sec. 6.3):
 """
 from __future__ import annotations
 
+import ctypes
+import os
+import subprocess
+import tempfile
+import threading
+
 import numpy as np
 
-__all__ = ["uniform", "permutation", "sortedness", "interleaved", "normal_f32",
+__all__ = ["uniform", "permutation", "sortedness", "sortedness_cached", "interleaved", "normal_f32",
            "index_payload", "segment_sizes", "offsets_of", "make"]
 
 
@@ -47,34 +53,98 @@ def permutation(n: int, seed: int, dtype=np.uint32) -> np.ndarray:
     return _rng(seed).permutation(n).astype(dtype)
 
 
-def sortedness(n: int, r: int, seed: int, dtype=np.uint32, batch: int | None = None) -> np.ndarray:
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SWAPS_SRC = os.path.join(_HERE, "swaps.c")
+_SWAPS_SO = os.path.join(_HERE, "_build", "libswaps.so")
+_swaps_lock = threading.Lock()
+_swaps_lib = None
+
+
+def build() -> str:
+    """Compiles the swap applier (plain C) that large sortedness inputs use."""
+    os.makedirs(os.path.dirname(_SWAPS_SO), exist_ok=True)
+    if not os.path.exists(_SWAPS_SO) or os.path.getmtime(_SWAPS_SO) < os.path.getmtime(_SWAPS_SRC):
+        tmp = _SWAPS_SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SWAPS_SRC])
+        os.replace(tmp, _SWAPS_SO)
+    return _SWAPS_SO
+
+
+def _swaps():
+    global _swaps_lib
+    with _swaps_lock:
+        if _swaps_lib is None:
+            L = ctypes.CDLL(build())
+            for f in (L.synth_apply_swaps_u32, L.synth_apply_swaps_u64):
+                f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+                f.restype = None
+            _swaps_lib = L
+    return _swaps_lib
+
+
+def _sortedness_batch_size(n: int) -> int:
+    return max(1, min(1 << 17, int(np.sqrt(n)) * 4))
+
+
+def sortedness(n: int, r: int, seed: int, dtype=np.uint32, batch: int | None = None,
+               native: bool | None = None) -> np.ndarray:
     """0..n-1 followed by r random pair swaps applied in order (Sec. 1).
 
-    Swaps are drawn in batches; within a batch, swaps that touch a position no
-    other swap of the batch touches commute with everything else in the batch
-    and are applied at once, the rest one by one in draw order, so the result
-    is exactly that of the r swaps applied sequentially.
+    Swaps are drawn in batches (i then j of every batch).  The numpy path
+    applies, within a batch, the swaps that touch a position no other swap of
+    the batch touches at once (they commute with everything else in the
+    batch) and the rest one by one in draw order; the native path (a small C
+    loop, used when ``native`` is true or, by default, for r >= 10^6) applies
+    every swap in draw order.  Both give exactly the result of the r swaps
+    applied sequentially, so they agree bit for bit.
     """
-    a = np.arange(n, dtype=dtype)
+    dt = np.dtype(dtype)
+    a = np.arange(n, dtype=dt)
     if n < 2 or r <= 0:
         return a
     g = _rng(seed)
     if batch is None:
-        batch = max(1, min(1 << 17, int(np.sqrt(n)) * 4))
+        batch = _sortedness_batch_size(n)
+    if native is None:
+        native = r >= 10**6 and dt in (np.dtype(np.uint32), np.dtype(np.uint64))
+    apply = None
+    if native:
+        L = _swaps()
+        apply = L.synth_apply_swaps_u32 if dt == np.dtype(np.uint32) else L.synth_apply_swaps_u64
     left = int(r)
     while left > 0:
         b = min(batch, left)
         i = g.integers(0, n, size=b, dtype=np.int64)
         j = g.integers(0, n, size=b, dtype=np.int64)
-        pos = np.concatenate([i, j])
-        uniq, counts = np.unique(pos, return_counts=True)
-        multi = uniq[counts > 1]
-        clash = np.isin(i, multi) | np.isin(j, multi)
-        gi, gj = i[~clash], j[~clash]
-        a[gi], a[gj] = a[gj], a[gi].copy()
-        for x, y in zip(i[clash].tolist(), j[clash].tolist()):
-            a[x], a[y] = a[y], a[x]
+        if apply is not None:
+            apply(a.ctypes.data, i.ctypes.data, j.ctypes.data, b)
+        else:
+            pos = np.concatenate([i, j])
+            uniq, counts = np.unique(pos, return_counts=True)
+            multi = uniq[counts > 1]
+            clash = np.isin(i, multi) | np.isin(j, multi)
+            gi, gj = i[~clash], j[~clash]
+            a[gi], a[gj] = a[gj], a[gi].copy()
+            for x, y in zip(i[clash].tolist(), j[clash].tolist()):
+                a[x], a[y] = a[y], a[x]
         left -= b
+    return a
+
+
+def sortedness_cached(n: int, r: int, seed: int, dtype=np.uint32) -> np.ndarray:
+    """sortedness(), stored once per (n, r, seed, dtype) in the system's
+    temporary directory, for the inputs that take a while to draw (r = 10^9 at
+    n = 10^8: about half a minute)."""
+    dt = np.dtype(dtype)
+    path = os.path.join(tempfile.gettempdir(), f"mms_sortedness_{n}_{r}_{seed}_{dt.name}.npy")
+    if os.path.exists(path):
+        a = np.load(path)
+        if a.shape == (n,) and a.dtype == dt:
+            return a
+    a = sortedness(n, r, seed, dt)
+    tmp = path + f".{os.getpid()}.tmp.npy"
+    np.save(tmp, a)
+    os.replace(tmp, path)
     return a
 
 

@@ -296,3 +296,19 @@ def test_planted_mistakes_are_caught(mutation):
     with oracle.mutation(mutation):
         assert not _pins_hold(), f"planted mistake {mutation} went unnoticed"
     assert _pins_hold()
+
+
+@pytest.mark.parametrize("threads", [2, 3, 8])
+def test_threaded_oracle_equals_the_serial_oracle(threads):
+    """The CPU baseline's all-cores variant splits the same recursion into
+    threads: it must return exactly the serial oracle's result."""
+    for n, mod in [(0, 0), (1, 0), (65535, 7), (65537, 0), (300001, 1000), (1 << 20, 3)]:
+        keys = synth.uniform(n, n + threads, np.uint32)
+        if mod:
+            keys = keys % np.uint32(mod)
+        vals = synth.index_payload(n)
+        a = oracle.sort(keys, vals)
+        b = oracle.sort_parallel(keys, vals, threads)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    f = synth.normal_f32(200000, 5)
+    assert np.array_equal(oracle.sort(f)[0].view(np.uint32), oracle.sort_parallel(f, None, threads)[0].view(np.uint32))
