@@ -18,21 +18,30 @@
 
 namespace mms {
 
-// Bitonic sorting network over a lane's 32 registers (ascending).
+// Sorting network over a lane's 32 registers (ascending): Batcher's odd-even
+// merge sort (K. E. Batcher, "Sorting networks and their applications",
+// AFIPS 1968), 191 compare-exchanges in 15 stages against the bitonic
+// sorter's 240.  Stage (p, k) of the network compares items x and x + k for
+// x = j + i with j running from k mod p in steps of 2k and i from 0 to k - 1,
+// whenever both lie in the same block of 2p items.  Every index is a
+// compile-time constant once the loops are unrolled, so each compare-exchange
+// is register to register; within a stage about two of three pairs take the
+// multiply-add form (by their ordinal in the stage), as in the other networks.
 template <typename KeyT>
 __device__ __forceinline__ void lane_sort32(KeyT (&v)[32], const MadOnes& c) {
 #pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
+  for (int lp = 0; lp < 5; ++lp) {
 #pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
+    for (int lk = lp; lk >= 0; --lk) {
+      const int p = 1 << lp, k = 1 << lk;
+      const int j0 = k & (p - 1);                      // first j of the stage: k mod p
+      int ord = 0;                                     // ordinal of the pair in its stage
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          if ((i & k) == 0)
-            cas_mix(v[i], v[ixj], pair_ordinal(i, j), c);
-          else
-            cas_mix(v[ixj], v[i], pair_ordinal(i, j), c);
+      for (int x = 0; x < 31; ++x) {                   // x = j + i, j = j0 + 2kt, i < k
+        if (x + k < 32 && x >= j0 && ((x - j0) & (2 * k - 1)) < k &&
+            (x >> (lp + 1)) == ((x + k) >> (lp + 1))) {
+          cas_mix(v[x], v[x + k], ord, c);
+          ++ord;
         }
       }
     }

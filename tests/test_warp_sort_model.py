@@ -147,3 +147,65 @@ def test_warp_sort_transposes_are_conflict_free():
                 assert len(groups) == 8 and len(set(groups)) == 8, (kind, q, groups)
         else:
             assert len(access) == 32 and len(set(access)) == 32, (kind, access)
+
+
+def odd_even_pairs(n):
+    """The lane network's compare-exchanges, in the loop order of lane_sort32
+    (tile_sort.cuh): Batcher's odd-even merge sort, stage (p, k) comparing x
+    and x + k for x = j + i, j from k mod p in steps of 2k, i < k, when both
+    lie in the same block of 2p items."""
+    out = []
+    p = 1
+    while p < n:
+        k = p
+        while k >= 1:
+            j = k % p
+            while j + k < n:
+                for i in range(k):
+                    x = j + i
+                    if x + k < n and x // (2 * p) == (x + k) // (2 * p):
+                        out.append((x, x + k))
+                j += 2 * k
+            k //= 2
+        p *= 2
+    return out
+
+
+def batcher_recursive(lo, n):
+    """Batcher's construction written recursively: sort both halves, then the
+    odd-even merge (merge the even and the odd subsequences, then compare
+    neighbours (2i-1, 2i))."""
+    def merge(lo, n, r):
+        step = 2 * r
+        if step < n:
+            yield from merge(lo, n, step)
+            yield from merge(lo + r, n, step)
+            for i in range(lo + r, lo + n - r, step):
+                yield (i, i + r)
+        else:
+            yield (lo, lo + r)
+    if n > 1:
+        m = n // 2
+        yield from batcher_recursive(lo, m)
+        yield from batcher_recursive(lo + m, m)
+        yield from merge(lo, n, 1)
+
+
+def test_lane_network_is_batchers_odd_even_merge_sort():
+    pairs = odd_even_pairs(32)
+    assert len(pairs) == 191                       # (p^2 - p + 4) 2^(p-2) - 1 for n = 2^5
+    assert sorted(pairs) == sorted(batcher_recursive(0, 32))
+    # 0-1 principle, exhaustively for the 16-input network of the same loops
+    p16 = odd_even_pairs(16)
+    x = ((np.arange(1 << 16)[:, None] >> np.arange(16)) & 1).astype(np.uint8)
+    for a, b in p16:
+        lo, hi = np.minimum(x[:, a], x[:, b]), np.maximum(x[:, a], x[:, b])
+        x[:, a], x[:, b] = lo, hi
+    assert np.all(np.diff(x.astype(np.int8), axis=1) >= 0)
+    # and random keys with many ties for the 32-input network
+    rng = np.random.default_rng(3)
+    y = rng.integers(0, 6, size=(20000, 32))
+    for a, b in pairs:
+        lo, hi = np.minimum(y[:, a], y[:, b]), np.maximum(y[:, a], y[:, b])
+        y[:, a], y[:, b] = lo, hi
+    assert np.all(np.diff(y, axis=1) >= 0)
