@@ -824,15 +824,20 @@ def main():
     n_ev = 2 + 2 * len(plan) + (1 if args.pairs else 0)
     stream = torch.cuda.current_stream()
 
-    def step(events=None):
+    def step(events=None, bounds=None):
         work.copy_(src)
         if args.pairs:
             vals.copy_(iota32)
+        if bounds:
+            bounds[0].record(stream)
+        if args.pairs:
             mms.sort_pairs(work, vals, fanout=args.fanout, workspace=ws, kt=kt, events=events,
                            tile_items=args.tile)
         else:
             mms.sort_keys(work, fanout=args.fanout, workspace=ws, kt=kt, events=events,
                           tile_items=args.tile)
+        if bounds:
+            bounds[1].record(stream)
 
     for _ in range(args.warmup):
         step()
@@ -845,24 +850,27 @@ def main():
     # Timed windows of exactly K steps each (barrier + synchronize on both
     # sides, max over ranks), repeated until they span --min-timed-s seconds so
     # that the clock record and the median rest on more than a few ms.
+    # Each step's events bracket the sort call only (the input restore is
+    # outside them); no event sits between the sort's own kernels, so each
+    # splitter and merge pass can launch programmatically behind the kernel
+    # before it.  Per-kernel times come from separate steps (below).
     sampler = ClockSampler(gpu_uuid(local))
     sampler.start()
     time.sleep(0.5)
     windows = []
-    stage = []
     t0 = time.time()
     while True:
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         for s_ in range(args.steps):
-            step(evs[s_])
+            step(bounds=evs[s_])
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        step_ms = [e[0].elapsed_time(e[-1]) for e in evs]
-        stage += [[e[i].elapsed_time(e[i + 1]) for i in range(n_ev - 1)] for e in evs]
+        step_ms = [a.elapsed_time(b) for a, b in evs]
         windows.append(aggregate_over_ranks(sum(step_ms), N, args.steps, world, dev))
         spent = sum(w[0] for w in windows) * args.steps / 1e3
         # every rank takes the same decision: the window times are max-reduced
@@ -875,6 +883,15 @@ def main():
         raise SystemExit("bench: sorted output is wrong after the timed windows")
     order = sorted(range(len(windows)), key=lambda i: windows[i][0])
     ms_per_step, value = windows[order[len(order) // 2]]          # the median window
+
+    # Per-kernel times: steps with an event after every kernel (which keeps
+    # each kernel from launching before the previous one has finished).
+    prof = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(20)]
+    for e in prof:
+        step(events=e)
+    torch.cuda.synchronize()
+    stage = [[e[i].elapsed_time(e[i + 1]) for i in range(n_ev - 1)] for e in prof]
+    staged_ms = statistics.median(e[0].elapsed_time(e[-1]) for e in prof)
 
     # per-kernel averages over every timed step: [tile_sort, (splitter, merge) per round,
     # (value gather for pairs)]
@@ -934,7 +951,10 @@ def main():
                           "gkeys_per_s": [w[1] for w in windows],
                           "note": "value and ms_per_step are the median window's"},
         "stages_ms": {"tile_sort": tile_ms, "splitter": split_ms, "merge_pass": merge_ms,
-                      "pairs_finalize": gather_ms, "dominant": dominant},
+                      "pairs_finalize": gather_ms, "dominant": dominant,
+                      "sort_ms_with_an_event_after_every_kernel": staged_ms,
+                      "note": "per-kernel means over 20 further steps that record an event after every "
+                              "kernel; the timed steps record events only around the sort call"},
         "roofline": roofline,
         "gpu_launches": len(windows) * args.steps * (1 + 2 * len(plan) + (1 if args.pairs else 0)),
         "gpu_launches_note": "kernels of the timed windows: base case, splitter and merge pass per round"

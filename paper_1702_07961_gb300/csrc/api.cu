@@ -3,6 +3,8 @@
 // the launch sequence of one sort: base case, then for every merge round the
 // splitter and the merge pass, ping-ponging between the caller's buffer and
 // the workspace copy so that the last round lands in the caller's buffer.
+// The splitters and merge passes are launched with programmatic stream
+// serialization, each right behind one of this library's kernels.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -354,12 +356,13 @@ mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws,
   long long run_len = S;
   for (int r = 0; r < rounds && st == MMS_OK; ++r) {
     const long long Sm = merge_tile_for(kb, tw, K[r], opt, n, run_len);
-    st = check_launch(mms::launch_splitter(kb, Sm, cur, (long long)n, run_len, K[r], table, s), "splitter");
+    st = check_launch(mms::launch_splitter(kb, Sm, cur, (long long)n, run_len, K[r], table, s, true),
+                      "splitter");
     mark();
     if (st != MMS_OK) break;
     st = check_launch(mms::launch_merge_pass(kb, tw, Sm, is_f32 && r == rounds - 1, cur, other,
                                              (long long)n, run_len, K[r], table, dev_err, s,
-                                             test_timeout),
+                                             test_timeout, true),
                       "merge_pass");
     mark();
     void* t = cur;
@@ -412,11 +415,12 @@ static mms_status pairs32_run(bool is_f32, void* d_keys, uint32_t* d_values, siz
   long long run_len = S;
   int cur = 0;
   for (int r = 0; r < rounds && st == MMS_OK; ++r) {
-    st = check_launch(mms::launch_splitter(8, S, comp[cur], (long long)n, run_len, K[r], table, s), "splitter");
+    st = check_launch(mms::launch_splitter(8, S, comp[cur], (long long)n, run_len, K[r], table, s, true),
+                      "splitter");
     mark();
     if (st != MMS_OK) break;
     st = check_launch(mms::launch_merge_pass(8, tw, S, false, comp[cur], comp[1 - cur], (long long)n,
-                                             run_len, K[r], table, dev_err, s), "merge_pass");
+                                             run_len, K[r], table, dev_err, s, false, true), "merge_pass");
     mark();
     cur = 1 - cur;
     run_len *= K[r];

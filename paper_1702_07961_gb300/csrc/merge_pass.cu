@@ -23,6 +23,8 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
     mbar_init(bar, 1);
     if (test_timeout) mbar_init(bar + 1, 1);   // the test hook's barrier (bar[1] is spare)
   }
+  griddep_wait();                                // the pivot table and the runs: earlier kernels'
+  griddep_launch_dependents();
   merge_tile<KeyT, WARPS>(in, out, n, run_len, K, g, j, table + t * K, table + (t + 1) * K, XOUT,
                           dev_err, smem_raw, bar, 0u, S, test_timeout != 0);
 }
@@ -30,7 +32,7 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
 template <typename KeyT, int WARPS, bool XOUT>
 static cudaError_t launch_merge_t(long long S, const void* in, void* out, long long n,
                                   long long run_len, int K, const long long* table, int* dev_err,
-                                  cudaStream_t s, bool test_timeout) {
+                                  cudaStream_t s, bool test_timeout, bool pdl) {
   const size_t smem = MergeGeom<KeyT, WARPS>::bytes(K);
   auto k = merge_pass_kernel<KeyT, WARPS, XOUT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -39,28 +41,27 @@ static cudaError_t launch_merge_t(long long S, const void* in, void* out, long l
   const long long ntiles = num_tiles(S, n, run_len, K);
   long long tpg = tiles_per_group(S, run_len, K);
   if (tpg > 0xFFFFFFFFll) tpg = 0xFFFFFFFFll;   // more than the grid: every tile is in group 0
-  k<<<(unsigned)ntiles, WARPS * 32, smem, s>>>(static_cast<const KeyT*>(in), static_cast<KeyT*>(out),
-                                              n, run_len, K, table, tpg, (int)S, dev_err,
-                                              test_timeout ? 1 : 0);
-  return cudaGetLastError();
+  return launch_k(k, dim3((unsigned)ntiles), dim3(WARPS * 32), smem, s, pdl,
+                  static_cast<const KeyT*>(in), static_cast<KeyT*>(out), n, run_len, K, table, tpg,
+                  (int)S, dev_err, test_timeout ? 1 : 0);
 }
 
 cudaError_t launch_merge_pass(int key_bytes, int tile_warps, long long S, bool xout, const void* in,
                               void* out, long long n, long long run_len, int K,
                               const long long* table, int* dev_err, cudaStream_t s,
-                              bool test_timeout) {
+                              bool test_timeout, bool pdl) {
   if (n <= 0) return cudaSuccess;
   if (key_bytes == 4) {
     if (tile_warps == 8)
-      return xout ? launch_merge_t<uint32_t, 8, true>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout)
-                  : launch_merge_t<uint32_t, 8, false>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout);
+      return xout ? launch_merge_t<uint32_t, 8, true>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout, pdl)
+                  : launch_merge_t<uint32_t, 8, false>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout, pdl);
     if (tile_warps == 4)
-      return xout ? launch_merge_t<uint32_t, 4, true>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout)
-                  : launch_merge_t<uint32_t, 4, false>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout);
+      return xout ? launch_merge_t<uint32_t, 4, true>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout, pdl)
+                  : launch_merge_t<uint32_t, 4, false>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout, pdl);
     return cudaErrorInvalidValue;
   }
-  if (tile_warps == 4) return launch_merge_t<uint64_t, 4, false>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout);
-  if (tile_warps == 2) return launch_merge_t<uint64_t, 2, false>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout);
+  if (tile_warps == 4) return launch_merge_t<uint64_t, 4, false>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout, pdl);
+  if (tile_warps == 2) return launch_merge_t<uint64_t, 2, false>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout, pdl);
   return cudaErrorInvalidValue;
 }
 

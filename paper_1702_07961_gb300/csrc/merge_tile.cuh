@@ -14,8 +14,10 @@
 //      the runs the group holds (the paper's minBlockHeap has the same
 //      levels), one level at a time: every
 //      tree node of the level (a pair of sequences) is cut into 1024-item
-//      output blocks, the blocks of the level are dealt to the warps, and a
-//      CTA barrier separates the levels.  A node's output is written into the
+//      output blocks, the blocks of the level are dealt to the warps (its
+//      full-size blocks first, then the small last blocks of its nodes,
+//      which a smaller network merges), and a CTA barrier separates the
+//      levels.  A node's output is written into the
 //      span its segments were staged in, alternating between two buffers by
 //      level; every segment span carries 32 items of slack so that a node's
 //      last, partial block can use its output region as transpose space.
@@ -29,9 +31,9 @@
 
 namespace mms {
 
-// Control area after a merge CTA's mbarrier: the merge-tree node table (8
+// Control area after a merge CTA's mbarrier: the merge-tree node table (10
 // fields x 32 nodes) and four scalars, written by warp 0 for the whole CTA.
-constexpr int kCtlNodeFields = 8;
+constexpr int kCtlNodeFields = 10;
 constexpr int kCtlScalars = 8;
 constexpr size_t kMergeCtlBytes = sizeof(int) * (kCtlNodeFields * 32 + kCtlScalars);
 
@@ -213,20 +215,44 @@ __device__ __forceinline__ void merge_plan_warp(const KeyT* __restrict__ in, lon
     const int lenA = is_node ? pm - pf : 0;
     const int lenB = is_node ? pl - pm : 0;
     const int nb = (lenA + lenB + kBlockItems - 1) / kBlockItems;
-    int fst = nb;
+    // A node's last block is "small" when it holds at most kSmallBlockMax
+    // items; it is merged by the small network, after every full-size block
+    // of its level, so that the level's big blocks are dealt first and the
+    // cheap ones fill in.  Work items of a level: its nodes' big blocks in
+    // node order, then its small blocks in node order; levels follow each
+    // other.  Inclusive scans over the nodes (lanes, in level order) of the
+    // big and the small block counts give every node its first big item and
+    // its small item: with n0 / n1 the first / last node of the node's level,
+    //   first big item = big blocks before the node + small blocks before n0,
+    //   small item     = big blocks up to n1 + small blocks before the node.
+    const int tail = lenA + lenB - (nb - 1) * kBlockItems;
+    const int small = (nb > 0 && tail <= kSmallBlockMax) ? 1 : 0;
+    const int nbig = nb - small;
+    int sbig = nbig, ssm = small;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int x = __shfl_up_sync(0xffffffffu, fst, o);
-      if (lane >= o) fst += x;
+      const int x = __shfl_up_sync(0xffffffffu, sbig, o);
+      const int y = __shfl_up_sync(0xffffffffu, ssm, o);
+      if (lane >= o) {
+        sbig += x;
+        ssm += y;
+      }
     }
+    const unsigned same_level = __match_any_sync(0xffffffffu, is_node ? c_level : -1);
+    const int n0 = __ffs(same_level) - 1, n1 = 31 - __clz(same_level);
+    const int small_before_n0 = __shfl_sync(0xffffffffu, ssm - small, n0);
+    const int big_upto_n1 = __shfl_sync(0xffffffffu, sbig, n1);
+    const int small_upto_n1 = __shfl_sync(0xffffffffu, ssm, n1);
     ctl[0 * 32 + lane] = lenA;
     ctl[1 * 32 + lane] = lenB;
     ctl[2 * 32 + lane] = (c_level == 1) ? rf + hf : rf;                     // staged segment
     ctl[3 * 32 + lane] = (mid < K) ? ((c_level == 1) ? rm + hm : rm) : 0;   // vs. child output
     ctl[4 * 32 + lane] = rf;                                                // output span
-    ctl[5 * 32 + lane] = fst - nb;                                          // first block
+    ctl[5 * 32 + lane] = (sbig - nbig) + small_before_n0;                  // first big item
     ctl[6 * 32 + lane] = nb;
     ctl[7 * 32 + lane] = is_node ? c_level : 0;
+    ctl[8 * 32 + lane] = small ? big_upto_n1 + (ssm - small) : -1;         // small item
+    ctl[9 * 32 + lane] = big_upto_n1 + small_upto_n1;                      // end of the level
     if (lane == 0) {
       ctl[kCtlNodeFields * 32 + 0] = nl;
       ctl[kCtlNodeFields * 32 + 1] = nnodes;
@@ -252,35 +278,48 @@ __device__ __forceinline__ void merge_levels(KeyT* bufX, KeyT* bufY, const int* 
   const int c_offA = ctl[2 * 32 + lane], c_offB = ctl[3 * 32 + lane];
   const int c_out = ctl[4 * 32 + lane], c_first = ctl[5 * 32 + lane];
   const int c_nb = ctl[6 * 32 + lane], c_level = ctl[7 * 32 + lane];
+  const int c_small = ctl[8 * 32 + lane], c_end = ctl[9 * 32 + lane];
+  const int c_nbig = c_nb - (c_small >= 0 ? 1 : 0);
 
-  // Level by level: the blocks of every node of level lv are dealt to the
-  // warps round-robin; a barrier ends the level.
+  // Level by level: the big blocks of the level's nodes, then their small
+  // last blocks, are dealt to the warps round-robin; a barrier ends the level.
   for (int lv = 1; lv <= nl; ++lv) {
     const unsigned lvm = __ballot_sync(0xffffffffu, is_node && c_level == lv);
     const int n0 = __ffs(lvm) - 1, n1 = 31 - __clz(lvm);
     const int it0 = __shfl_sync(0xffffffffu, c_first, n0);
-    const int it1 = __shfl_sync(0xffffffffu, c_first + c_nb, n1);
+    const int it1 = __shfl_sync(0xffffffffu, c_end, n0);
+    const int big_end = __shfl_sync(0xffffffffu, c_first + c_nbig, n1);
     const KeyT* src = (lv & 1) ? bufX : bufY;           // level lv reads level lv-1's buffer
     KeyT* dst = (lv & 1) ? bufY : bufX;
     for (int item = it0 + warp; item < it1; item += WARPS) {
-      const unsigned sel = __ballot_sync(0xffffffffu, is_node && c_first <= item && c_nb > 0);
-      const int c = 31 - __clz(sel);
+      int c, blk;
+      if (item < big_end) {                            // a big block: the node whose range holds it
+        const unsigned sel = __ballot_sync(0xffffffffu, is_node && c_first <= item && c_nbig > 0);
+        c = 31 - __clz(sel);
+        blk = item - __shfl_sync(0xffffffffu, c_first, c);
+      } else {                                         // a small block: its node's last
+        c = __ffs(__ballot_sync(0xffffffffu, is_node && c_small == item)) - 1;
+        blk = __shfl_sync(0xffffffffu, c_nb, c) - 1;
+      }
       const int lenA = __shfl_sync(0xffffffffu, c_lenA, c);
       const int lenB = __shfl_sync(0xffffffffu, c_lenB, c);
       const int offA = __shfl_sync(0xffffffffu, c_offA, c);
       const int offB = __shfl_sync(0xffffffffu, c_offB, c);
       const int outo = __shfl_sync(0xffffffffu, c_out, c);
-      const int fi = __shfl_sync(0xffffffffu, c_first, c);
       const KeyT* A = src + offA;
       const KeyT* B = src + offB;
       const int L = lenA + lenB;
-      const int d0 = (item - fi) * kBlockItems;
+      const int d0 = blk * kBlockItems;
       const int m = (L - d0) < kBlockItems ? (L - d0) : kBlockItems;
       const int a0 = warp_corank(A, lenA, B, lenB, d0, lane);
       const int a1 = (d0 + m == L) ? lenA : warp_corank(A, lenA, B, lenB, d0 + m, lane, a0, a0 + m);
       const int X = a1 - a0;
-      warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, lane,
-                             xout && lv == nl);
+      if (m <= kSmallBlockMax)
+        warp_merge_small<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, lane,
+                               xout && lv == nl);
+      else
+        warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, lane,
+                               xout && lv == nl);
       __syncwarp();
     }
     sync();

@@ -80,6 +80,15 @@ __device__ __forceinline__ void cas(KeyT& a, KeyT& b) {
   a = lo;
   b = hi;
 }
+// 64-bit keys: one unsigned 64-bit compare drives the four 32-bit selects of
+// the pair (min and max computed apart would each compare and select).
+__device__ __forceinline__ void cas(uint64_t& a, uint64_t& b) {
+  const bool sw = b < a;
+  const uint64_t lo = sw ? b : a;
+  const uint64_t hi = sw ? a : b;
+  a = lo;
+  b = hi;
+}
 
 // Compare-exchange whose direction is chosen per lane: with flip set the
 // larger key goes to a.  Flipping the stages of a bitonic merge whose stride
@@ -90,6 +99,15 @@ __device__ __forceinline__ void cas_dir(KeyT& a, KeyT& b, bool flip) {
   const KeyT x = a, y = b;
   a = flip ? kmax(x, y) : kmin(x, y);
   b = flip ? kmin(x, y) : kmax(x, y);
+}
+// 64-bit keys: the direction folds into the compare's predicate (swap when
+// the pair is out of the lane's order), then four 32-bit selects.
+__device__ __forceinline__ void cas_dir(uint64_t& a, uint64_t& b, bool flip) {
+  const bool sw = (b < a) != flip;
+  const uint64_t x = sw ? b : a;
+  const uint64_t y = sw ? a : b;
+  a = x;
+  b = y;
 }
 
 // ---------------------------------------------------------------------------
@@ -455,6 +473,71 @@ __device__ __forceinline__ void warp_merge_block(const KeyT* A, int X, const Key
 }
 
 // ---------------------------------------------------------------------------
+// Warp merge of a small block (X + Y = m <= 32 R items, R in {1, 2, 4, 8}):
+// the same bitonic merge of C = A ascending ++ pads ++ B descending, over
+// 32 R items instead of 1024.  Register k of lane l holds C[32k + l]; the
+// half-cleaners of stride >= 32 run between registers, those of stride < 32
+// between lanes through shuffles (one shuffle and a min or max per register),
+// and register k is stored to out[32k + l].  Every shared-memory access is 32
+// consecutive items: conflict-free.  A merge tree's node ends in such a block
+// whenever its size lies just above a multiple of 1024 -- on random inputs
+// about half of a tile's nodes -- and this network costs a fraction of the
+// 1024-item one.  `out` receives exactly m items (no transpose space).
+// ---------------------------------------------------------------------------
+constexpr int kSmallBlockMax = 256;
+
+template <int R, typename KeyT>
+__device__ __forceinline__ void warp_merge_small_r(const KeyT* A, int X, const KeyT* B, int Y,
+                                                   KeyT* out, int lane, bool xout) {
+  constexpr int n = 32 * R;
+  const int m = X + Y;
+  const KeyT* pa = A + lane;                         // C[32k+lane] = A[32k+lane]
+  const KeyT* pb = B + (n - 1 - lane);               // C[32k+lane] = B[n-1-32k-lane]
+  const int xa = X - lane;                           // 32k + lane < X  <=>  32k < xa
+  const int xb = n - Y - lane;                       // 32k + lane >= n - Y  <=>  32k >= xb
+  KeyT v[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    KeyT t = key_pad<KeyT>();
+    lds_if_lt(t, pa + 32 * k, 32 * k, xa);
+    lds_if_ge(t, pb - 32 * k, 32 * k, xb);
+    v[k] = t;
+  }
+#pragma unroll
+  for (int s = R / 2; s >= 1; s >>= 1) {             // strides 16R .. 32: between registers
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+      if ((k & s) == 0) cas(v[k], v[k + s]);
+  }
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {                // strides 16 .. 1: between lanes
+    const bool upper = (lane & s) != 0;              // the pair's larger index keeps the max
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const KeyT y = __shfl_xor_sync(0xffffffffu, v[k], s);
+      v[k] = upper ? kmax(v[k], y) : kmin(v[k], y);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int idx = 32 * k + lane;
+    if (idx < m) out[idx] = xout ? (KeyT)ordered_to_f32((uint32_t)v[k]) : v[k];
+  }
+}
+
+// Merges A[0, X) and B[0, Y) (X + Y <= kSmallBlockMax) into out[0, X + Y)
+// with the smallest network that holds them.
+template <typename KeyT>
+__device__ __forceinline__ void warp_merge_small(const KeyT* A, int X, const KeyT* B, int Y,
+                                                 KeyT* out, int lane, bool xout) {
+  const int m = X + Y;
+  if (m <= 32) warp_merge_small_r<1>(A, X, B, Y, out, lane, xout);
+  else if (m <= 64) warp_merge_small_r<2>(A, X, B, Y, out, lane, xout);
+  else if (m <= 128) warp_merge_small_r<4>(A, X, B, Y, out, lane, xout);
+  else warp_merge_small_r<8>(A, X, B, Y, out, lane, xout);
+}
+
+// ---------------------------------------------------------------------------
 // One CTA merge level with a barrier after it (used by the base case, whose
 // blocks are all full).  Sequence q (q < 32) of `src` is described by lane
 // q's (off, len); sequences (2p, 2p+1) are merged into `dst`, pair outputs
@@ -575,6 +658,21 @@ __device__ __forceinline__ void bulk_s2g_and_wait(void* dst_gmem, const void* sr
 
 __device__ __forceinline__ void set_device_error(int* err, int code) {
   if (err) atomicCAS(err, kDevOk, code);
+}
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch (sm_90 and later).  The sort's kernels after
+// the base case are launched with programmatic stream serialization: a grid
+// may be scheduled once every CTA of the kernel before it has started, so its
+// CTAs become resident while that kernel's last wave drains.
+// griddep_wait() then blocks until the previous grid has completed and its
+// memory is visible; every such kernel calls it before its first global
+// memory access (reads and writes alike).  For a normal launch both are
+// no-ops.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 }  // namespace mms

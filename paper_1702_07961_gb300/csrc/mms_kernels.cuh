@@ -64,20 +64,49 @@ cudaError_t launch_u64_pairs_final(const void* kcopy, const void* vcopy, const v
                                    void* keys, void* vals, long long n, cudaStream_t s);
 
 // Splitter: co-ranks of every output tile start (tiles of S items) of every
-// group of K runs.
+// group of K runs.  pdl as for launch_merge_pass.
 cudaError_t launch_splitter(int key_bytes, long long S, const void* in, long long n,
-                            long long run_len, int K, long long* table, cudaStream_t s);
+                            long long run_len, int K, long long* table, cudaStream_t s,
+                            bool pdl = false);
 
 // One K-way merge round driven by the splitter table; output tiles of S
 // items (a multiple of 1024, at most 1024 * tile_warps).  test_timeout: the
 // test hook of mms_options.test_flags (every CTA's extra wait runs out).
+// pdl: launch with programmatic stream serialization (the previous kernel on
+// the stream is one of this library's).
 cudaError_t launch_merge_pass(int key_bytes, int tile_warps, long long S, bool xout, const void* in,
                               void* out, long long n, long long run_len, int K,
                               const long long* table, int* dev_err, cudaStream_t s,
-                              bool test_timeout = false);
+                              bool test_timeout = false, bool pdl = false);
 
 // Records the detail message mms_last_error_detail() returns on this thread.
 void set_error_detail(const char* msg);
+
+// Launches `kernel` on `s`, with programmatic stream serialization when `pdl`
+// (the kernel must call griddep_wait() before its first global memory access;
+// see mms_common.cuh).  Where the stream or device refuses the attribute, the
+// launch is repeated without it.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+  if (e != cudaSuccess && pdl && (e == cudaErrorNotSupported || e == cudaErrorInvalidValue)) {
+    (void)cudaGetLastError();
+    cfg.numAttrs = 0;
+    e = cudaLaunchKernelEx(&cfg, kernel, args...);
+  }
+  return e;
+}
 
 // Output tiles of a round: every group of K runs (K * run_len items, the last
 // group possibly short) is cut into tiles of S items, the last tile of every

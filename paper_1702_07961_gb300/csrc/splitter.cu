@@ -11,23 +11,26 @@ __global__ void __launch_bounds__(128)
   const int lane = threadIdx.x & 31;
   const int gb = lane & ~(W - 1);                 // first lane of this lane group
   const unsigned gm = W == 32 ? 0xffffffffu : (((1u << W) - 1u) << gb);
+  griddep_wait();                                 // the runs are the previous kernel's output
+  griddep_launch_dependents();
   const long long t = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / W) + gb / W;
   if (t >= ntiles) return;                        // uniform over the lane group
   splitter_row<KeyT, W, Idx>(in, n, run_len, K, S, t / tpg, t % tpg, table + t * K, gm, gb);
 }
 
 template <typename KeyT, int W>
-static void launch_w(const void* in, long long n, long long run_len, int K, long long S, long long tpg,
-                     long long ntiles, long long* table, cudaStream_t s) {
+static cudaError_t launch_w(const void* in, long long n, long long run_len, int K, long long S,
+                            long long tpg, long long ntiles, long long* table, cudaStream_t s,
+                            bool pdl) {
   const long long per_block = 4 * (32 / W);       // 4 warps of 32 / W tiles each
   const unsigned grid = (unsigned)((ntiles + per_block - 1) / per_block);
+  const KeyT* kin = static_cast<const KeyT*>(in);
   // 32-bit counts and positions while no probe can pass 2^31 (n < 2^30)
   if (n < (1ll << 30))
-    splitter_kernel<KeyT, W, int><<<grid, 128, 0, s>>>(static_cast<const KeyT*>(in), n, run_len, K, S,
-                                                       tpg, ntiles, table);
-  else
-    splitter_kernel<KeyT, W, long long><<<grid, 128, 0, s>>>(static_cast<const KeyT*>(in), n, run_len,
-                                                             K, S, tpg, ntiles, table);
+    return launch_k(splitter_kernel<KeyT, W, int>, dim3(grid), dim3(128), 0, s, pdl, kin, n, run_len,
+                    K, S, tpg, ntiles, table);
+  return launch_k(splitter_kernel<KeyT, W, long long>, dim3(grid), dim3(128), 0, s, pdl, kin, n,
+                  run_len, K, S, tpg, ntiles, table);
 }
 
 // One output tile per warp (W = 32).  Packing 32 / W tiles into a warp's lane
@@ -35,21 +38,14 @@ static void launch_w(const void* in, long long n, long long run_len, int K, long
 // K = 4 against 0.47 ms): the search is bound by the latency of its
 // dependent loads and needs the independent warps, and lane groups of one
 // warp diverge in their per-tile pop loops.
-template <typename KeyT>
-static void launch_k(const void* in, long long n, long long run_len, int K, long long S, long long tpg,
-                     long long ntiles, long long* table, cudaStream_t s) {
-  launch_w<KeyT, 32>(in, n, run_len, K, S, tpg, ntiles, table, s);
-}
-
 cudaError_t launch_splitter(int key_bytes, long long S, const void* in, long long n,
-                            long long run_len, int K, long long* table, cudaStream_t s) {
+                            long long run_len, int K, long long* table, cudaStream_t s, bool pdl) {
   const long long ntiles = num_tiles(S, n, run_len, K);
   if (ntiles <= 0) return cudaSuccess;
   if (K < 2 || K > kMaxFanout) return cudaErrorInvalidValue;
   const long long tpg = tiles_per_group(S, run_len, K);
-  if (key_bytes == 4) launch_k<uint32_t>(in, n, run_len, K, S, tpg, ntiles, table, s);
-  else launch_k<uint64_t>(in, n, run_len, K, S, tpg, ntiles, table, s);
-  return cudaGetLastError();
+  if (key_bytes == 4) return launch_w<uint32_t, 32>(in, n, run_len, K, S, tpg, ntiles, table, s, pdl);
+  return launch_w<uint64_t, 32>(in, n, run_len, K, S, tpg, ntiles, table, s, pdl);
 }
 
 }  // namespace mms

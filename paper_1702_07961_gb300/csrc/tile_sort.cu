@@ -9,6 +9,7 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
     tile_sort_kernel(const KeyT* __restrict__ in, KeyT* out, long long n) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   constexpr int T = WARPS * kBlockItems;
+  griddep_launch_dependents();                    // the first splitter may get resident early
   tile_sort_tile<KeyT, WARPS, XIN>(in, out, n, (long long)blockIdx.x * T, XOUT, smem_raw);
 }
 
@@ -19,6 +20,7 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<uint64_t, WARPS>::value
     tile_sort_composite_kernel(const uint32_t* __restrict__ in, uint64_t* out, long long n) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   constexpr int T = WARPS * kBlockItems;
+  griddep_launch_dependents();
   tile_sort_composite_tile<WARPS, XIN>(in, out, n, (long long)blockIdx.x * T, 0, smem_raw);
 }
 

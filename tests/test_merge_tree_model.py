@@ -92,3 +92,72 @@ def test_tree_over_the_runs_a_group_holds(K):
             nl, res = run_tree(segs, K, kruns)
             assert nl == math.ceil(math.log2(max(kruns, 2)))
             assert np.array_equal(res, np.sort(np.concatenate(segs)))
+
+
+BLOCK = 1024
+SMALL_MAX = 256
+
+
+def block_items(levels, sizes):
+    """The plan's numbering of a tile's work items (merge_plan_warp): per node
+    (lanes in level order) its first big item, its small item (or -1) and its
+    level's end, from inclusive scans of the big and small block counts."""
+    n = len(sizes)
+    nb = [-(-L // BLOCK) for L in sizes]
+    small = [1 if (b > 0 and L - (b - 1) * BLOCK <= SMALL_MAX) else 0 for L, b in zip(sizes, nb)]
+    nbig = [b - s for b, s in zip(nb, small)]
+    sbig = np.cumsum(nbig)
+    ssm = np.cumsum(small)
+    first, sitem, end = [], [], []
+    for q in range(n):
+        same = [i for i in range(n) if levels[i] == levels[q]]
+        n0, n1 = same[0], same[-1]
+        first.append(int(sbig[q] - nbig[q] + ssm[n0] - small[n0]))
+        sitem.append(int(sbig[n1] + ssm[q] - small[q]) if small[q] else -1)
+        end.append(int(sbig[n1] + ssm[n1]))
+    return nb, nbig, small, first, sitem, end
+
+
+def test_level_items_deal_big_blocks_first_then_small_ones():
+    """merge_levels' item -> (node, block) lookup over the plan's numbering:
+    every block of every node of a level is one item of that level's range,
+    exactly once; the level's full-size blocks come first, its small last
+    blocks (at most 256 items) after them; the levels' ranges follow each
+    other from 0."""
+    rng = np.random.default_rng(11)
+    for trial in range(400):
+        K = int(rng.choice([2, 3, 4, 5, 8, 16, 32]))
+        nl, nodes = node_table(K, int(rng.integers(1, K + 1)))
+        levels = [lv for lv, _ in nodes]
+        kind = trial % 4
+        if kind == 0:        # sizes near multiples of 1024, as on random keys
+            sizes = [int(max(0, BLOCK * rng.integers(0, 9) + rng.integers(-60, 60))) for _ in nodes]
+        elif kind == 1:      # exact multiples (sorted or interleaved inputs)
+            sizes = [int(BLOCK * rng.integers(0, 9)) for _ in nodes]
+        else:
+            sizes = [int(rng.integers(0, 8193)) for _ in nodes]
+        nb, nbig, small, first, sitem, end = block_items(levels, sizes)
+        start = 0
+        for lv in range(1, nl + 1):
+            lvn = [q for q in range(len(nodes)) if levels[q] == lv]
+            n0, n1 = lvn[0], lvn[-1]
+            it0, it1 = first[n0], end[n0]
+            big_end = first[n1] + nbig[n1]
+            assert it0 == start
+            got = []
+            for item in range(it0, it1):
+                if item < big_end:
+                    c = max(q for q in range(len(nodes)) if first[q] <= item and nbig[q] > 0)
+                    blk = item - first[c]
+                    assert not (small[c] and blk == nb[c] - 1)
+                else:
+                    cs = [q for q in range(len(nodes)) if sitem[q] == item]
+                    assert len(cs) == 1
+                    c = cs[0]
+                    blk = nb[c] - 1
+                    assert sizes[c] - blk * BLOCK <= SMALL_MAX
+                assert levels[c] == lv
+                got.append((c, blk))
+            want = [(q, b) for q in lvn for b in range(nb[q])]
+            assert sorted(got) == sorted(want) and len(set(got)) == len(got)
+            start = it1
