@@ -97,8 +97,8 @@ int tile_warps_for(int key_bytes, const mms_options* opt) {
 // every round's K instead; the result does not depend on the plan.
 namespace plan_model {
 // ms per 10^8 items of one round (merge pass + splitter), for K = 2, 4, 8, 16, 32
-constexpr double kCost4[5] = {0.230, 0.356, 0.518, 0.723, 1.134};   // 4-byte keys
-constexpr double kCost8[5] = {0.519, 1.001, 1.514, 2.262, 3.940};   // 8-byte keys / composites
+constexpr double kCost4[5] = {0.221, 0.332, 0.465, 0.621, 1.001};   // 4-byte keys
+constexpr double kCost8[5] = {0.466, 0.727, 1.035, 1.566, 2.873};   // 8-byte keys / composites
 constexpr double kLaunchMs = 0.010;                                 // two launches per round
 }  // namespace plan_model
 
