@@ -311,15 +311,29 @@ __device__ __forceinline__ void merge_levels(KeyT* bufX, KeyT* bufY, const int* 
       const int L = lenA + lenB;
       const int d0 = blk * kBlockItems;
       const int m = (L - d0) < kBlockItems ? (L - d0) : kBlockItems;
-      const int a0 = warp_corank(A, lenA, B, lenB, d0, lane);
-      const int a1 = (d0 + m == L) ? lenA : warp_corank(A, lenA, B, lenB, d0 + m, lane, a0, a0 + m);
-      const int X = a1 - a0;
-      if (m <= kSmallBlockMax)
-        warp_merge_small<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, lane,
-                               xout && lv == nl);
-      else
-        warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, lane,
-                               xout && lv == nl);
+      if (lenA != 0 && lenB != 0) {
+        const int a0 = warp_corank(A, lenA, B, lenB, d0, lane);
+        const int a1 =
+            (d0 + m == L) ? lenA : warp_corank(A, lenA, B, lenB, d0 + m, lane, a0, a0 + m);
+        const int X = a1 - a0;
+        if (m <= kSmallBlockMax)
+          warp_merge_small<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, lane,
+                                 xout && lv == nl);
+        else
+          warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, lane,
+                                 xout && lv == nl);
+      } else {
+        // One child is empty (a node over runs past the group's last, or a
+        // tile that takes nothing from one side): the block is a copy, made
+        // with 32 consecutive keys per access instead of a merge network.
+        const KeyT* from = (lenB == 0 ? A : B) + d0;
+        KeyT* to = dst + outo + d0;
+        const bool xo = xout && lv == nl;
+        for (int i = lane; i < m; i += 32) {
+          const KeyT v = from[i];
+          to[i] = xo ? (KeyT)ordered_to_f32((uint32_t)v) : v;
+        }
+      }
       __syncwarp();
     }
     sync();

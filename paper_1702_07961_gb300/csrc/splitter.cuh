@@ -86,11 +86,24 @@ __device__ __forceinline__ unsigned lanes_with_min(unsigned gm, bool cond, uint6
 // (pad, key, run)); -1 if none.  Lane numbers are the warp's.
 template <typename KeyT>
 __device__ __forceinline__ int grp_argmax(unsigned gm, bool cond, const Item<KeyT>& it) {
-  const unsigned any = __ballot_sync(gm, cond);
-  if (!any) return -1;
-  const unsigned pads = __ballot_sync(gm, cond && it.pad);
-  if (pads) return 31 - __clz(pads);
-  return 31 - __clz(lanes_with_max(gm, cond, it.key));
+  if constexpr (sizeof(KeyT) == 4) {
+    // One max over the keys with pads raised to the all-ones key, then the
+    // lanes holding that maximum: a pad among them wins (pads come after
+    // every real key, an all-ones real key included), else the highest lane
+    // (the largest run index).  The pad ballot does not wait for the max.
+    const uint32_t kk = cond ? (it.pad ? 0xffffffffu : (uint32_t)it.key) : 0u;
+    const uint32_t mx = grp_max_u32(gm, kk);
+    const unsigned padm = __ballot_sync(gm, cond && it.pad);
+    const unsigned m = __ballot_sync(gm, cond && kk == mx);
+    const unsigned mp = m & padm;
+    return m ? 31 - __clz(mp ? mp : m) : -1;
+  } else {
+    const unsigned any = __ballot_sync(gm, cond);
+    if (!any) return -1;
+    const unsigned pads = __ballot_sync(gm, cond && it.pad);
+    if (pads) return 31 - __clz(pads);
+    return 31 - __clz(lanes_with_max(gm, cond, it.key));
+  }
 }
 
 template <typename KeyT>
