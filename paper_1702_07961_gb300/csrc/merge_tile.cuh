@@ -320,7 +320,7 @@ __device__ __forceinline__ void merge_levels(KeyT* bufX, KeyT* bufY, const int* 
           warp_merge_small<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, lane,
                                  xout && lv == nl);
         else
-          warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, lane,
+          warp_merge_block<KeyT, MergeMix>(A + a0, X, B + (d0 - a0), m - X, dst + outo + d0, lane,
                                  xout && lv == nl);
       } else {
         // One child is empty (a node over runs past the group's last, or a

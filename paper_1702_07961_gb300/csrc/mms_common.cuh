@@ -115,19 +115,28 @@ __device__ __forceinline__ void cas_dir(uint64_t& a, uint64_t& b, bool flip) {
 // the ALU pipe and integer multiply-add on the FMA pipe; on sm_103a both are
 // half rate.  The larger key of a pair is also a + b - min(a, b), exact
 // modulo 2^32, so a compare-exchange can take one ALU min and two multiply-adds
-// instead of a min and a max.  Mixing the two forms about 2 : 1 keeps both
-// pipes and the issue slot busy: measured 1.41x the compare-exchange rate of
-// min/max alone (1.38x for the per-lane-direction form).  The multiply-adds
-// use a runtime 1 (and -1, -2) so that the compiler keeps them multiplies.
-// 64-bit keys take min/max only.
+// instead of a min and a max.  Mixing the two forms keeps both pipes and the
+// issue slot busy: in a register-only microbenchmark 11 of 16 pairs in the
+// multiply-add form gave 1.41x the compare-exchange rate of min/max alone
+// (10 of 16 for the per-lane-direction form, 1.38x).  Inside the kernels the
+// best mix follows what else the kernel issues, measured on GB300: the base
+// case (issue-bound, ALU pipe 69% busy) is fastest with 6 of 16 plain pairs
+// and 10 of 16 direction pairs, the merge pass (barrier-bound, ALU 57%) with
+// plain pairs as min/max and 10 of 16 direction pairs; each kernel passes its
+// own Mix type.  The multiply-adds use a runtime 1 (and -1, -2) so that the
+// compiler keeps them multiplies.  64-bit keys take min/max only.
 // ---------------------------------------------------------------------------
-struct MadOnes {
+// MIX / MIXD: how many of a stage's 16 pairs take the multiply-add form, for
+// plain pairs and for pairs whose direction is chosen per lane.
+template <int MIX, int MIXD>
+struct Mix {
   uint32_t one, m1, m2;   // 1, -1, -2 (mod 2^32), unknown to the compiler
 };
-__device__ __forceinline__ MadOnes mad_ones() {
+template <typename M>
+__device__ __forceinline__ M mad_ones() {
   const uint32_t b = blockDim.x;
   const uint32_t one = b >> (31 - __clz(b));   // b >> floor(log2 b) == 1 for b >= 1
-  return MadOnes{one, 0u - one, 0u - one - one};
+  return M{one, 0u - one, 0u - one - one};
 }
 __device__ __forceinline__ uint32_t mad_u32(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t d;
@@ -135,19 +144,21 @@ __device__ __forceinline__ uint32_t mad_u32(uint32_t a, uint32_t b, uint32_t c) 
   return d;
 }
 
-// Which pairs of a stage (ordinal i among the stage's 16 pairs of a lane) use
-// the multiply-add form: 11 of 16 for plain pairs, 10 of 16 for pairs whose
-// direction is chosen per lane -- the measured balance points.
-__device__ __forceinline__ constexpr bool mad_form(int i) { return i % 3 != 2; }
-__device__ __forceinline__ constexpr bool mad_form_dir(int i) { return i % 7 < 4 || i >= 14; }
+// Whether the pair with ordinal i among a stage's 16 pairs takes the
+// multiply-add form when `count` of 16 do: the pairs are spread evenly
+// (i * count mod 16 below count).
+__device__ __forceinline__ constexpr bool mad_pick(int i, int count) {
+  return ((i * count) & 15) < count;
+}
 // Ordinal of the pair (k, k + s) among the 16 pairs of a stride-s stage.
 __device__ __forceinline__ constexpr int pair_ordinal(int k, int s) {
   return (k & (s - 1)) | ((k >> 1) & ~(s - 1));
 }
 
 // Compare-exchange (ascending) of a stage pair with ordinal i.
-__device__ __forceinline__ void cas_mix(uint32_t& a, uint32_t& b, int i, const MadOnes& c) {
-  if (mad_form(i)) {
+template <int MIX, int MIXD>
+__device__ __forceinline__ void cas_mix(uint32_t& a, uint32_t& b, int i, const Mix<MIX, MIXD>& c) {
+  if (mad_pick(i, MIX)) {
     const uint32_t lo = min(a, b);
     const uint32_t s = mad_u32(a, c.one, b);
     a = lo;
@@ -156,12 +167,16 @@ __device__ __forceinline__ void cas_mix(uint32_t& a, uint32_t& b, int i, const M
     cas(a, b);
   }
 }
-__device__ __forceinline__ void cas_mix(uint64_t& a, uint64_t& b, int, const MadOnes&) { cas(a, b); }
+template <int MIX, int MIXD>
+__device__ __forceinline__ void cas_mix(uint64_t& a, uint64_t& b, int, const Mix<MIX, MIXD>&) {
+  cas(a, b);
+}
 
 // cas_dir with the direction as f in {0, 1} (1: the larger key goes to a).
+template <int MIX, int MIXD>
 __device__ __forceinline__ void cas_dir_mix(uint32_t& a, uint32_t& b, uint32_t f, int i,
-                                            const MadOnes& c) {
-  if (mad_form_dir(i)) {
+                                            const Mix<MIX, MIXD>& c) {
+  if (mad_pick(i, MIXD)) {
     const uint32_t lo = min(a, b);
     const uint32_t s = mad_u32(a, c.one, b);   // a + b
     const uint32_t d = mad_u32(lo, c.m2, s);   // max - min
@@ -172,10 +187,15 @@ __device__ __forceinline__ void cas_dir_mix(uint32_t& a, uint32_t& b, uint32_t f
     cas_dir(a, b, f != 0);
   }
 }
+template <int MIX, int MIXD>
 __device__ __forceinline__ void cas_dir_mix(uint64_t& a, uint64_t& b, uint32_t f, int,
-                                            const MadOnes&) {
+                                            const Mix<MIX, MIXD>&) {
   cas_dir(a, b, f != 0);
 }
+
+// The mixes the kernels use (multiply-add pairs of 16: plain, per-lane direction).
+using TileMix = Mix<kTileMadPairs, kTileMadDirPairs>;
+using MergeMix = Mix<kMergeMadPairs, kMergeMadDirPairs>;
 
 
 // ---------------------------------------------------------------------------
@@ -322,8 +342,8 @@ __device__ __forceinline__ int flip_mask(int lane) {
 
 // Half-cleaners of register distance D, D/2, .., 1 (strides 32D .. 32 of the
 // striped layout), ascending.
-template <int D, typename KeyT>
-__device__ __forceinline__ void striped_stages(KeyT (&v)[32], const MadOnes& c) {
+template <int D, typename KeyT, typename M>
+__device__ __forceinline__ void striped_stages(KeyT (&v)[32], const M& c) {
 #pragma unroll
   for (int s = D; s >= 1; s >>= 1) {
 #pragma unroll
@@ -361,8 +381,8 @@ __device__ __forceinline__ void striped_to_blocked(KeyT (&v)[32], KeyT* out, int
 // the strides of 16 bytes and more run in the direction of the lane's
 // flip_mask bit, leaving register j with item 32l + (j ^ flip_mask(l)) -- the
 // layout warp_store_block writes out; otherwise all ascending.
-template <bool FLIP, typename KeyT>
-__device__ __forceinline__ void blocked_stages(KeyT (&v)[32], int lane, const MadOnes& c) {
+template <bool FLIP, typename KeyT, typename M>
+__device__ __forceinline__ void blocked_stages(KeyT (&v)[32], int lane, const M& c) {
   constexpr int E = Vec16<KeyT>::E;
   const int F = flip_mask<KeyT>(lane);
 #pragma unroll
@@ -387,10 +407,10 @@ __device__ __forceinline__ void blocked_stages(KeyT (&v)[32], int lane, const Ma
 // padding.  After the five half-cleaners of stride >= 32 the rows are ordered
 // (every item of row k is <= every item of row k+1), so rows at or above
 // nr = ceil(m / 32) hold only pads (or real all-ones keys, bit-identical to
-// pads) and are neither stored nor loaded.
-template <typename KeyT>
+// pads) and are neither stored nor loaded.  M: the kernel's compare-exchange mix.
+template <typename M, typename KeyT>
 __device__ __forceinline__ void warp_bitonic_1024(KeyT (&v)[32], KeyT* out, int nr, int lane) {
-  const MadOnes c = mad_ones();
+  const M c = mad_ones<M>();
   striped_stages<16>(v, c);                          // strides 512 .. 32
   striped_to_blocked(v, out, nr, lane);
   blocked_stages<true>(v, lane, c);                  // strides 16 .. 1, store layout
@@ -463,12 +483,13 @@ __device__ __forceinline__ void warp_store_block(KeyT* out, int m, KeyT (&v)[32]
 
 // `out` is 16-byte aligned; the warp may use out[0, 32 * ceil((X + Y) / 32))
 // as transpose space, so up to 31 items past the block's end must be free.
-template <typename KeyT>
+// M: the calling kernel's compare-exchange mix.
+template <typename KeyT, typename M>
 __device__ __forceinline__ void warp_merge_block(const KeyT* A, int X, const KeyT* B, int Y,
                                                  KeyT* out, int lane, bool xout) {
   KeyT v[32];
   warp_load_bitonic(A, X, B, Y, v, lane);
-  warp_bitonic_1024(v, out, (X + Y + 31) >> 5, lane);
+  warp_bitonic_1024<M>(v, out, (X + Y + 31) >> 5, lane);
   warp_store_block<KeyT>(out, X + Y, v, lane, xout);
 }
 
@@ -545,7 +566,7 @@ __device__ __forceinline__ void warp_merge_small(const KeyT* A, int X, const Key
 // blocks of every pair, dealt to the warps round-robin.  next_seq() gives the
 // descriptors of the outputs.
 // ---------------------------------------------------------------------------
-template <typename KeyT>
+template <typename KeyT, typename M>
 __device__ __forceinline__ void cta_merge_level(const KeyT* src, KeyT* dst, int my_off, int my_len,
                                                 int nseq, int warp, int nwarps, int lane,
                                                 bool xout) {
@@ -566,7 +587,7 @@ __device__ __forceinline__ void cta_merge_level(const KeyT* src, KeyT* dst, int 
       const int a0 = warp_corank(A, a_len, B, b_len, d0, lane);
       const int a1 = (d0 + m == L) ? a_len : warp_corank(A, a_len, B, b_len, d0 + m, lane, a0, a0 + m);
       const int X = a1 - a0;
-      warp_merge_block<KeyT>(A + a0, X, B + (d0 - a0), m - X, dst + outoff + d0, lane, xout);
+      warp_merge_block<KeyT, M>(A + a0, X, B + (d0 - a0), m - X, dst + outoff + d0, lane, xout);
     }
     outoff += (L + E - 1) / E * E;
   }

@@ -27,8 +27,8 @@ namespace mms {
 // compile-time constant once the loops are unrolled, so each compare-exchange
 // is register to register; within a stage about two of three pairs take the
 // multiply-add form (by their ordinal in the stage), as in the other networks.
-template <typename KeyT>
-__device__ __forceinline__ void lane_sort32(KeyT (&v)[32], const MadOnes& c) {
+template <typename KeyT, typename M>
+__device__ __forceinline__ void lane_sort32(KeyT (&v)[32], const M& c) {
 #pragma unroll
   for (int lp = 0; lp < 5; ++lp) {
 #pragma unroll
@@ -79,9 +79,9 @@ __device__ __forceinline__ void blocked_to_striped_rev(KeyT (&v)[32], KeyT* scra
 
 // One level of the warp sort: every block of R rows, whose two halves are
 // each sorted, becomes sorted (blocked layout in and out).
-template <int R, typename KeyT>
+template <int R, typename KeyT, typename M>
 __device__ __forceinline__ void warp_merge_rows(KeyT (&v)[32], KeyT* scratch, int lane,
-                                                const MadOnes& c) {
+                                                const M& c) {
   blocked_to_striped_rev<R>(v, scratch, lane);
   striped_stages<R / 2>(v, c);                       // strides 16R .. 32
   striped_to_blocked(v, scratch, 32, lane);
@@ -97,7 +97,7 @@ __device__ __forceinline__ void warp_merge_rows(KeyT (&v)[32], KeyT* scratch, in
 // flip_mask(l)), the layout warp_store_block writes out.
 template <typename KeyT>
 __device__ __forceinline__ void warp_sort_1024(KeyT (&v)[32], KeyT* scratch, int lane) {
-  const MadOnes c = mad_ones();
+  const TileMix c = mad_ones<TileMix>();
   lane_sort32(v, c);
   warp_merge_rows<2>(v, scratch, lane, c);
   warp_merge_rows<4>(v, scratch, lane, c);
@@ -170,7 +170,8 @@ __device__ __forceinline__ void tile_sort_finish(KeyT (&v)[32], KeyT* out, long 
   KeyT* dst = bufY;
   int nseq = WARPS;
   while (nseq > 1) {
-    cta_merge_level<KeyT>(src, dst, my_off, my_len, nseq, warp, WARPS, lane, xout && nseq <= 2);
+    cta_merge_level<KeyT, TileMix>(src, dst, my_off, my_len, nseq, warp, WARPS, lane,
+                                   xout && nseq <= 2);
     next_seq<KeyT>(my_off, my_len, nseq, lane);
     nseq = (nseq + 1) >> 1;
     __syncthreads();
