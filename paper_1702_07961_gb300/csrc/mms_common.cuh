@@ -121,8 +121,8 @@ __device__ __forceinline__ void cas_dir(uint64_t& a, uint64_t& b, bool flip) {
 // (10 of 16 for the per-lane-direction form, 1.38x).  Inside the kernels the
 // best mix follows what else the kernel issues, measured on GB300: the base
 // case (issue-bound, ALU pipe 69% busy) is fastest with 6 of 16 plain pairs
-// and 10 of 16 direction pairs, the merge pass (barrier-bound, ALU 57%) with
-// plain pairs as min/max and 10 of 16 direction pairs; each kernel passes its
+// and 12 of 16 direction pairs, the merge pass (barrier-bound, ALU 57%) with
+// plain pairs as min/max and 12 of 16 direction pairs; each kernel passes its
 // own Mix type.  The multiply-adds use a runtime 1 (and -1, -2) so that the
 // compiler keeps them multiplies.  64-bit keys take min/max only.
 // ---------------------------------------------------------------------------

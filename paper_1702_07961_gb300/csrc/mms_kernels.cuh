@@ -16,8 +16,8 @@ constexpr int kMaxFanout = 32;
 // Compare-exchange pairs (of every 16 in a network stage) computed as one
 // min and two multiply-adds instead of min and max, per kernel: the base
 // case and the merge pass (plain pairs, pairs with a per-lane direction).
-constexpr int kTileMadPairs = 6, kTileMadDirPairs = 10;
-constexpr int kMergeMadPairs = 0, kMergeMadDirPairs = 10;
+constexpr int kTileMadPairs = 6, kTileMadDirPairs = 12;
+constexpr int kMergeMadPairs = 0, kMergeMadDirPairs = 12;
 
 // Device error word values (the first word of a sort workspace).
 constexpr int kDevOk = 0;
