@@ -991,76 +991,110 @@ def main():
         roofline["per_pass_frac_by_fanout"] = by_k
 
     if not args.no_e2e and headline:
-        # End to end through the public API: every step copies its input from
-        # pinned host memory, sorts it (mms_sort_keys) and copies the result
-        # back to pinned host memory.  --e2e-slots slots (device buffer,
-        # workspace, stream, host result) take the steps in turn, so uploads
-        # and downloads overlap other steps' sorts -- how a pipeline of sorts
-        # uses the library.  Each slot's stream runs upload, sort, download in
-        # order, so with two slots that chain bounds the rate; three let the
-        # sorts run back to back.  The one-at-a-time figure is reported beside.
+        # End to end through the public API, as a three-stage pipeline: every
+        # step uploads its input from pinned host memory (upload stream), sorts
+        # it with mms_sort_keys (compute stream, one sort after another), and
+        # downloads the result to pinned host memory (download stream).  Events
+        # order each step's three stages, and a buffer slot is reused only after
+        # its previous download has finished, so uploads and downloads of other
+        # steps overlap the sorts.  --e2e-slots device buffers are in flight.
+        # The one-at-a-time figure (upload, sort, download, wait) is reported
+        # beside.
         h_in = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
         iota_np = np.arange(N, dtype=np.uint32)
-        ns = max(1, args.e2e_slots)
-        slots = [{"work": work if i == 0 else torch.empty_like(work),
-                  "ws": ws if i == 0 else torch.zeros_like(ws), "stream": torch.cuda.Stream(),
-                  "out": torch.empty_like(h_in).pin_memory()} for i in range(ns)]
+        ns = max(2, args.e2e_slots)
+        up, comp, down = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        bufs = [work] + [torch.empty_like(work) for _ in range(ns - 1)]
+        outs = [torch.empty_like(h_in).pin_memory() for _ in range(ns)]
+        freed = [None] * ns                                  # download of the slot's last step done
+        last = [None] * ns
 
-        def e2e_step(sl):
-            with torch.cuda.stream(sl["stream"]):
-                sl["work"].copy_(h_in, non_blocking=True)
-                mms.sort_keys(sl["work"], fanout=args.fanout, workspace=sl["ws"], kt=mms.KEY_U32,
-                              tile_items=args.tile, stream=sl["stream"])
-                sl["out"].copy_(sl["work"], non_blocking=True)
+        def e2e_step(i):
+            j = i % ns
+            loaded, sorted_ = torch.cuda.Event(), torch.cuda.Event()
+            done = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(up):
+                if freed[j] is not None:
+                    up.wait_event(freed[j])
+                bufs[j].copy_(h_in, non_blocking=True)
+                loaded.record(up)
+            with torch.cuda.stream(comp):
+                comp.wait_event(loaded)
+                mms.sort_keys(bufs[j], fanout=args.fanout, workspace=ws, kt=mms.KEY_U32,
+                              tile_items=args.tile, stream=comp)
+                sorted_.record(comp)
+            with torch.cuda.stream(down):
+                down.wait_event(sorted_)
+                outs[j].copy_(bufs[j], non_blocking=True)
+                done.record(down)
+            freed[j] = done
+            last[j] = i
 
         torch.cuda.synchronize()
         for i in range(2 * ns):                             # warm-up of every slot
-            e2e_step(slots[i % ns])
+            e2e_step(i)
         torch.cuda.synchronize()
         n_e2e = max(12, args.steps // 2)
-        # Several windows of n_e2e steps (host copies are the noisy part of
-        # this figure); the median window is reported, every window listed.
         e2e_windows = []
         ok = True
-        for w in range(5):
+        for w in range(7):
             start = torch.cuda.Event(enable_timing=True)
-            start.record(slots[0]["stream"])
-            for sl in slots[1:]:
-                sl["stream"].wait_event(start)
+            start.record(up)
+            comp.wait_event(start)
+            down.wait_event(start)
             for i in range(n_e2e):
-                e2e_step(slots[i % ns])
-            ends = []
-            for sl in slots:
-                e = torch.cuda.Event(enable_timing=True)
-                e.record(sl["stream"])
-                ends.append(e)
+                e2e_step(i)
+            end = torch.cuda.Event(enable_timing=True)
+            end.record(down)                                # the last step's download is the last work
             torch.cuda.synchronize()
-            e2e_windows.append(max(start.elapsed_time(e) for e in ends) / n_e2e)
-            ok = ok and all(bool(np.array_equal(sl["out"].numpy().view(np.uint32), iota_np)) for sl in slots)
+            e2e_windows.append(start.elapsed_time(end) / n_e2e)
+            ok = ok and all(bool(np.array_equal(o.numpy().view(np.uint32), iota_np)) for o in outs)
             if w >= 2 and sum(e2e_windows) * n_e2e / 1e3 >= args.min_timed_s:
                 break
         pipe_ms = statistics.median(e2e_windows)
         # one at a time: upload, sort, download, then the next step
         ser = []
-        sl = slots[0]
         for i in range(max(3, args.steps // 10)):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(sl["stream"])
-            e2e_step(sl)
-            b.record(sl["stream"])
+            a.record(comp)
+            with torch.cuda.stream(comp):
+                bufs[0].copy_(h_in, non_blocking=True)
+                mms.sort_keys(bufs[0], fanout=args.fanout, workspace=ws, kt=mms.KEY_U32,
+                              tile_items=args.tile, stream=comp)
+                outs[0].copy_(bufs[0], non_blocking=True)
+            b.record(comp)
             torch.cuda.synchronize()
             ser.append(a.elapsed_time(b))
         ser_ms = statistics.mean(ser)
-        ok = ok and bool(np.array_equal(sl["out"].numpy().view(np.uint32), iota_np))
+        ok = ok and bool(np.array_equal(outs[0].numpy().view(np.uint32), iota_np))
+        # The copies alone, for the record of which stage bounds the pipeline:
+        # host copy bandwidth on this machine varies between and within runs.
+        def copy_ms(fn):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ts = []
+            for _ in range(3):
+                a.record(comp)
+                with torch.cuda.stream(comp):
+                    fn()
+                b.record(comp)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            return statistics.median(ts)
+        h2d_ms = copy_ms(lambda: bufs[0].copy_(h_in, non_blocking=True))
+        d2h_ms = copy_ms(lambda: outs[0].copy_(bufs[0], non_blocking=True))
         out["e2e"] = {"value": N / (pipe_ms / 1e3) / 1e9 * world, "unit": UNIT,
                       "h2d_bytes_per_step": N * KEY_BYTES, "d2h_bytes_per_step": N * KEY_BYTES,
                       "ms_per_step": pipe_ms, "steps": n_e2e,
                       "windows_gkeys_per_s": [N / (m / 1e3) / 1e9 * world for m in e2e_windows],
                       "verified_last_output_of_every_slot": ok,
-                      "mode": f"{ns} slots taking the steps in turn: uploads and downloads overlap other "
-                              "steps' sorts",
-                      "one_at_a_time": {"value": N / (ser_ms / 1e3) / 1e9 * world, "ms_per_step": ser_ms}}
-        del slots
+                      "mode": f"pipeline: upload, sort and download streams, {ns} device buffers in flight; "
+                              "sorts back to back, copies overlapping them",
+                      "one_at_a_time": {"value": N / (ser_ms / 1e3) / 1e9 * world, "ms_per_step": ser_ms},
+                      "copies_alone": {"h2d_ms": h2d_ms, "d2h_ms": d2h_ms,
+                                       "h2d_gbs": N * KEY_BYTES / (h2d_ms / 1e3) / 1e9,
+                                       "d2h_gbs": N * KEY_BYTES / (d2h_ms / 1e3) / 1e9,
+                                       "note": "the pipeline is bound by max(sort, upload, download) per step"}}
+        del bufs, outs
 
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = time_oracle(keys_np, min(args.cpu_sample, N))
