@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--fanout", type=int, default=0, help="merge fanout K (0 = planner)")
     p.add_argument("--tile", type=int, default=0, help="tile items (0 = library default)")
     p.add_argument("--pairs", action="store_true", help="key + uint32 index payload (stable key-value sort)")
+    p.add_argument("--merge-variant", default="tree", choices=["tree", "partition"],
+                   help="merge rounds: the CTA merge tree (default) or the heap-free partition variant")
     p.add_argument("--key", default="u32", choices=["u32", "u64", "f32"],
                    help="sort workload: key type (the headline is u32)")
     p.add_argument("--input", default="permutation", choices=["permutation", "sortedness", "interleaved"],
@@ -827,6 +829,7 @@ def main():
     plan = mms.plan(kt, N, args.fanout, args.tile, pairs=args.pairs)
     n_ev = 2 + 2 * len(plan) + (1 if args.pairs else 0)
     stream = torch.cuda.current_stream()
+    mv = mms.MERGE_PARTITION if args.merge_variant == "partition" else mms.MERGE_TREE
 
     def step(events=None, bounds=None):
         work.copy_(src)
@@ -836,10 +839,10 @@ def main():
             bounds[0].record(stream)
         if args.pairs:
             mms.sort_pairs(work, vals, fanout=args.fanout, workspace=ws, kt=kt, events=events,
-                           tile_items=args.tile)
+                           tile_items=args.tile, merge_variant=mv)
         else:
             mms.sort_keys(work, fanout=args.fanout, workspace=ws, kt=kt, events=events,
-                          tile_items=args.tile)
+                          tile_items=args.tile, merge_variant=mv)
         if bounds:
             bounds[1].record(stream)
 
@@ -925,7 +928,9 @@ def main():
         achieved = bytes_pass / (merge_avg / 1e3) / 1e9
     else:
         achieved = bytes_pass / (tile_ms / 1e3) / 1e9
-    headline = args.key == "u32" and not args.pairs and args.input == "permutation"
+    headline = (args.key == "u32" and not args.pairs and args.input == "permutation"
+                and args.merge_variant == "tree")
+    partition_run = args.merge_variant == "partition" and args.key == "u32" and not args.pairs
     traffic = load_traffic(N, "merge_pass_kernel") if headline and merge_avg else None
     roofline = {"bound": "hbm", "kernel": "merge_pass" if merge_avg else "tile_sort",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -939,7 +944,8 @@ def main():
         roofline["tile_sort_traffic"] = load_traffic(N, "tile_sort_kernel")
 
     out = {
-        "metric": METRIC if headline else f"Gkeys/s at {N} {args.key}" + (" pairs" if args.pairs else ""),
+        "metric": METRIC if headline else (f"Gkeys/s at {N} {args.key}" + (" pairs" if args.pairs else "")
+                                           + (" (partition merge)" if args.merge_variant == "partition" else "")),
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.key, "data": "synthetic",
@@ -948,6 +954,7 @@ def main():
                                + ", one sort per step",
                    "global_batch": N * world, "seq_len": None, "parallelism": f"replicas{world}",
                    "plan_fanouts": plan, "tile": args.tile or mms.tile_items(kt),
+                   "merge_variant": args.merge_variant,
                    "l2": f"input {N * kb / 1e6:.0f} MB > 129 MB L2; a device copy restores the input "
                          "before every step, outside the timed events" if N * kb > 129e6 else
                          "input fits in L2"},
@@ -971,15 +978,15 @@ def main():
     # ceil(log2 K) on-chip tree levels per HBM read and write.  Measure the
     # merge pass alone at K = 2 and K = 4 too (same workload, same timing).
     by_k = {}
-    if headline:
-        for kf in (2, 4):
+    if headline or partition_run:
+        for kf in ((2, 4) if headline else (2, 4, 8, 16)):
             planf = mms.plan(kt, N, kf, args.tile)
             nf = 2 + 2 * len(planf)
             evf = [[torch.cuda.Event(enable_timing=True) for _ in range(nf)] for _ in range(10)]
             for i in range(13):
                 work.copy_(src)
                 mms.sort_keys(work, fanout=kf, workspace=ws, kt=kt, tile_items=args.tile,
-                              events=evf[i - 3] if i >= 3 else None)
+                              events=evf[i - 3] if i >= 3 else None, merge_variant=mv)
             torch.cuda.synchronize()
             # merge pass of round r: from event 2 + 2r (after its splitter) to 3 + 2r
             mf = statistics.mean(statistics.mean(e[2 + 2 * r].elapsed_time(e[3 + 2 * r])

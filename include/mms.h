@@ -75,10 +75,19 @@ typedef struct {
                         completes, then records MMS_ERR_TIMEOUT and stops: the device-side
                         failure path, with nothing left in flight.  The output is then
                         unspecified. */
-  int reserved;
+  int merge_variant; /* how a merge round merges a tile: MMS_MERGE_TREE (0, the default):
+                        the CTA's binary tree of block merges, level by level (Sec. 4.2);
+                        MMS_MERGE_PARTITION: the heap-free variant of Sec. 7 (future
+                        work), each warp finding its 1024-key output block's pieces in
+                        the tile's K segments by the partitioning search of Sec. 4.1 and
+                        merging them alone.  Same results; the partition variant takes
+                        the default tile geometry only (tile_items and merge_tile_items
+                        0) and applies to mms_sort_keys_ex and mms_sort_pairs_ex. */
 } mms_options;
 
 #define MMS_TEST_STAGING_TIMEOUT 1
+#define MMS_MERGE_TREE 0
+#define MMS_MERGE_PARTITION 1
 
 /* Bytes of workspace mms_sort_keys / mms_sort_pairs need for n keys: one
  * ping-pong copy of the keys (and values), the pivot table of the largest
@@ -163,6 +172,16 @@ mms_status mms_splitter(mms_key_type kt, const void* d_in, size_t n, size_t run_
 mms_status mms_merge_pass(mms_key_type kt, const void* d_in, void* d_out, size_t n,
                           size_t run_len, int K, const int64_t* d_table, void* d_ws,
                           size_t ws_bytes, void* stream);
+
+/* The same round merged by the heap-free partition variant (Sec. 7, future
+ * work; mms_options.merge_variant = MMS_MERGE_PARTITION): every output tile
+ * is cut into 1024-key blocks whose pieces in the tile's K segments the
+ * warps find with the search of Sec. 4.1 in shared memory, and each warp
+ * merges its own pieces.  Arguments, layout, ownership and errors as for
+ * mms_merge_pass; the output is identical. */
+mms_status mms_merge_pass_partition(mms_key_type kt, const void* d_in, void* d_out, size_t n,
+                                    size_t run_len, int K, const int64_t* d_table, void* d_ws,
+                                    size_t ws_bytes, void* stream);
 
 /* ---- batched (segmented) sorting ------------------------------------------- */
 

@@ -41,12 +41,17 @@ class _Options(ctypes.Structure):
     _fields_ = [("fanout", ctypes.c_int), ("num_events", ctypes.c_int),
                 ("events", ctypes.POINTER(ctypes.c_void_p)), ("tile_items", ctypes.c_int),
                 ("merge_tile_items", ctypes.c_int), ("test_flags", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("merge_variant", ctypes.c_int)]
 
 
 # mms_options.test_flags: a test hook that makes every merge CTA's extra
 # bounded wait run out (MMS_TEST_STAGING_TIMEOUT).
 TEST_STAGING_TIMEOUT = 1
+
+# mms_options.merge_variant: the CTA merge tree (default) or the heap-free
+# partition variant (MMS_MERGE_TREE, MMS_MERGE_PARTITION).
+MERGE_TREE = 0
+MERGE_PARTITION = 1
 
 
 class _SegOptions(ctypes.Structure):
@@ -94,6 +99,8 @@ def load() -> ctypes.CDLL:
         L.mms_splitter.restype = i32
         L.mms_merge_pass.argtypes = [i32, vp, vp, sz, sz, i32, vp, vp, sz, vp]
         L.mms_merge_pass.restype = i32
+        L.mms_merge_pass_partition.argtypes = [i32, vp, vp, sz, sz, i32, vp, vp, sz, vp]
+        L.mms_merge_pass_partition.restype = i32
         L.mms_sort_keys_noalloc.argtypes = [i32, vp, sz, vp]
         L.mms_sort_keys_noalloc.restype = i32
         L.mms_segmented_workspace_bytes.argtypes = [i32, sz, sz, i32, ctypes.POINTER(_SegOptions)]
@@ -147,12 +154,13 @@ def _ptr(t):
 
 
 def _opts(fanout: int, events=None, stream=None, tile_items: int = 0, merge_tile_items: int = 0,
-          test_flags: int = 0):
+          test_flags: int = 0, merge_variant: int = 0):
     o = _Options()
     o.fanout = int(fanout)
     o.tile_items = int(tile_items)
     o.merge_tile_items = int(merge_tile_items)
     o.test_flags = int(test_flags)
+    o.merge_variant = int(merge_variant)
     if events:
         for e in events:
             if not e.cuda_event:          # torch creates the CUDA event on first record
@@ -184,30 +192,32 @@ def plan(kt: int, n: int, fanout: int = 0, tile_items: int = 0, pairs: bool = Fa
 
 
 def sort_keys(keys, fanout: int = 0, workspace=None, stream=None, kt: int | None = None, events=None,
-              tile_items: int = 0, merge_tile_items: int = 0, test_flags: int = 0):
+              tile_items: int = 0, merge_tile_items: int = 0, test_flags: int = 0,
+              merge_variant: int = MERGE_TREE):
     """Sorts a contiguous CUDA tensor of keys in place; returns it.
 
     ``events``: optional list of ``torch.cuda.Event(enable_timing=True)``; the
     library records them before the first kernel and after each kernel.
     ``test_flags``: test hooks (``TEST_STAGING_TIMEOUT``), 0 in normal use.
+    ``merge_variant``: ``MERGE_TREE`` or ``MERGE_PARTITION``.
     """
     assert keys.is_cuda and keys.is_contiguous()
     kt = key_type_of(keys) if kt is None else kt
     n = keys.numel()
     ws_ptr, ws_len = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
-    o = _opts(fanout, events, stream, tile_items, merge_tile_items, test_flags)
+    o = _opts(fanout, events, stream, tile_items, merge_tile_items, test_flags, merge_variant)
     _check(load().mms_sort_keys_ex(kt, _ptr(keys), n, ws_ptr, ws_len, _stream_handle(stream), ctypes.byref(o)))
     return keys
 
 
 def sort_pairs(keys, values, fanout: int = 0, workspace=None, stream=None, kt: int | None = None,
-               events=None, tile_items: int = 0):
+               events=None, tile_items: int = 0, merge_variant: int = MERGE_TREE):
     """Stable sort of (key, 32-bit value) pairs in place (4-byte keys)."""
     assert keys.is_cuda and values.is_cuda and keys.numel() == values.numel()
     assert keys.is_contiguous() and values.is_contiguous() and values.element_size() == 4
     kt = key_type_of(keys) if kt is None else kt
     ws_ptr, ws_len = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
-    o = _opts(fanout, events, stream, tile_items)
+    o = _opts(fanout, events, stream, tile_items, merge_variant=merge_variant)
     _check(load().mms_sort_pairs_ex(kt, _ptr(keys), _ptr(values), keys.numel(), ws_ptr, ws_len,
                                     _stream_handle(stream), ctypes.byref(o)))
     return keys, values
@@ -248,12 +258,15 @@ def splitter(data, run_len: int, K: int, table=None, stream=None, kt: int | None
     return table
 
 
-def merge_pass(inp, out, run_len: int, K: int, table, workspace=None, stream=None, kt: int | None = None):
-    """One K-way merge round of ``inp`` into ``out`` driven by ``table``."""
+def merge_pass(inp, out, run_len: int, K: int, table, workspace=None, stream=None, kt: int | None = None,
+               merge_variant: int = MERGE_TREE):
+    """One K-way merge round of ``inp`` into ``out`` driven by ``table``
+    (``mms_merge_pass``, or ``mms_merge_pass_partition`` for MERGE_PARTITION)."""
     kt = key_type_of(inp) if kt is None else kt
     ws_ptr, ws_len = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
-    _check(load().mms_merge_pass(kt, _ptr(inp), _ptr(out), inp.numel(), run_len, K, _ptr(table),
-                                 ws_ptr, ws_len, _stream_handle(stream)))
+    fn = load().mms_merge_pass_partition if merge_variant == MERGE_PARTITION else load().mms_merge_pass
+    _check(fn(kt, _ptr(inp), _ptr(out), inp.numel(), run_len, K, _ptr(table),
+              ws_ptr, ws_len, _stream_handle(stream)))
     return out
 
 

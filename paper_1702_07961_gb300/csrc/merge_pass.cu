@@ -1,5 +1,6 @@
 // merge_pass.cu -- one K-way merge round over a whole array: one CTA per
-// output tile, running the CTA body of merge_tile.cuh.
+// output tile, running the CTA body of merge_tile.cuh (the CTA merge tree, or
+// the heap-free partition variant).
 #include "merge_tile.cuh"
 
 namespace mms {
@@ -8,7 +9,7 @@ size_t merge_pass_smem_bytes(int key_bytes, int warps, int K) {
   return merge_pass_smem_bytes_impl(key_bytes, warps, K);
 }
 
-template <typename KeyT, int WARPS, bool XOUT>
+template <typename KeyT, int WARPS, bool XOUT, bool PART>
 __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
     merge_pass_kernel(const KeyT* __restrict__ in, KeyT* __restrict__ out, long long n,
                       long long run_len, int K, const long long* __restrict__ table,
@@ -25,16 +26,16 @@ __global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
   }
   griddep_wait();                                // the pivot table and the runs: earlier kernels'
   griddep_launch_dependents();
-  merge_tile<KeyT, WARPS>(in, out, n, run_len, K, g, j, table + t * K, table + (t + 1) * K, XOUT,
-                          dev_err, smem_raw, bar, 0u, S, test_timeout != 0);
+  merge_tile<KeyT, WARPS, PART>(in, out, n, run_len, K, g, j, table + t * K, table + (t + 1) * K,
+                                XOUT, dev_err, smem_raw, bar, 0u, S, test_timeout != 0);
 }
 
-template <typename KeyT, int WARPS, bool XOUT>
+template <typename KeyT, int WARPS, bool XOUT, bool PART = false>
 static cudaError_t launch_merge_t(long long S, const void* in, void* out, long long n,
                                   long long run_len, int K, const long long* table, int* dev_err,
                                   cudaStream_t s, bool test_timeout, bool pdl) {
-  const size_t smem = MergeGeom<KeyT, WARPS>::bytes(K);
-  auto k = merge_pass_kernel<KeyT, WARPS, XOUT>;
+  const size_t smem = PART ? MergeGeom<KeyT, WARPS>::bytes_partition(K) : MergeGeom<KeyT, WARPS>::bytes(K);
+  auto k = merge_pass_kernel<KeyT, WARPS, XOUT, PART>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (S < kBlockItems || S > (long long)WARPS * kBlockItems || S % kBlockItems) return cudaErrorInvalidValue;
@@ -49,8 +50,15 @@ static cudaError_t launch_merge_t(long long S, const void* in, void* out, long l
 cudaError_t launch_merge_pass(int key_bytes, int tile_warps, long long S, bool xout, const void* in,
                               void* out, long long n, long long run_len, int K,
                               const long long* table, int* dev_err, cudaStream_t s,
-                              bool test_timeout, bool pdl) {
+                              bool test_timeout, bool pdl, bool partition) {
   if (n <= 0) return cudaSuccess;
+  if (partition) {   // the heap-free variant: default tile geometry only
+    if (tile_warps != default_tile_warps(key_bytes)) return cudaErrorInvalidValue;
+    if (key_bytes == 4)
+      return xout ? launch_merge_t<uint32_t, 8, true, true>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout, pdl)
+                  : launch_merge_t<uint32_t, 8, false, true>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout, pdl);
+    return launch_merge_t<uint64_t, 4, false, true>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout, pdl);
+  }
   if (key_bytes == 4) {
     if (tile_warps == 8)
       return xout ? launch_merge_t<uint32_t, 8, true>(S, in, out, n, run_len, K, table, dev_err, s, test_timeout, pdl)

@@ -28,6 +28,7 @@
 
 #include "mms_common.cuh"
 #include "mms_kernels.cuh"
+#include "splitter.cuh"
 
 namespace mms {
 
@@ -51,18 +52,23 @@ struct MergeGeom {
   __host__ __device__ static constexpr size_t bytes(int K) {
     return sizeof(KeyT) * 2 * (size_t)cap(K) + 16 + kMergeCtlBytes;
   }
+  // The partition variant adds its pivot rows after the control area: row b
+  // (b <= WARPS) holds, per segment, the items of the tile's first 1024 b
+  // outputs.
+  static constexpr size_t kRowBytes = sizeof(int) * 32 * (WARPS + 1);
+  __host__ __device__ static constexpr size_t bytes_partition(int K) { return bytes(K) + kRowBytes; }
 };
 
-inline size_t merge_pass_smem_bytes_impl(int key_bytes, int warps, int K) {
+inline size_t merge_pass_smem_bytes_impl(int key_bytes, int warps, int K, bool partition = false) {
   if (key_bytes == 4) {
     switch (warps) {
-      case 4: return MergeGeom<uint32_t, 4>::bytes(K);
-      case 8: return MergeGeom<uint32_t, 8>::bytes(K);
+      case 4: return partition ? MergeGeom<uint32_t, 4>::bytes_partition(K) : MergeGeom<uint32_t, 4>::bytes(K);
+      case 8: return partition ? MergeGeom<uint32_t, 8>::bytes_partition(K) : MergeGeom<uint32_t, 8>::bytes(K);
     }
   } else {
     switch (warps) {
-      case 2: return MergeGeom<uint64_t, 2>::bytes(K);
-      case 4: return MergeGeom<uint64_t, 4>::bytes(K);
+      case 2: return partition ? MergeGeom<uint64_t, 2>::bytes_partition(K) : MergeGeom<uint64_t, 2>::bytes(K);
+      case 4: return partition ? MergeGeom<uint64_t, 4>::bytes_partition(K) : MergeGeom<uint64_t, 4>::bytes(K);
     }
   }
   return 0;
@@ -348,6 +354,132 @@ __device__ __forceinline__ void merge_levels(KeyT* bufX, KeyT* bufY, const int* 
   for (int i = body + (int)threadIdx.x; i < m; i += WARPS * 32) dstg[i] = res[i];
 }
 
+// The heap-free variant of the merge (Sec. 7, future work: multiway merging
+// driven by the parallel partitioning alone, with no merge tree shared by the
+// CTA).  The tile's output is cut into 1024-item blocks, one per warp.
+//   1. Warp b finds the pivots of block start 1024 b in every staged segment
+//      with the splitter's own search (the multi-sequence selection of
+//      Sec. 4.1, multiseq_pivot, here over shared memory), and writes them as
+//      row b of `rows`; one CTA barrier publishes the rows.
+//   2. The warp's block is then the merge of its K pieces (segment r from
+//      row b to row b + 1), which the warp merges alone: pairs of pieces, then
+//      pairs of their outputs, along the same binary tree over the runs as the
+//      CTA tree, with no barrier between its levels.  The first level reads the
+//      staged pieces and writes its outputs packed into the warp's own
+//      1024-item region of bufY; later levels merge adjacent outputs back into
+//      their own span.  Merges of at most 1024 items at any offset take the
+//      register-and-shuffle network of the smallest power of two that holds
+//      them (warp_merge_any); the last level, whose output is the whole block
+//      at its 16-byte aligned start, takes the transposed 1024-item network.
+// bufX holds the staged segments (the node table's level-1 entries give each
+// segment's span), bufY receives the tile; the final store is the same as the
+// tree's.
+// A warp whose pivot rows do not describe pieces inside their segments that
+// add up to its block records kDevErrInternal in dev_err and merges nothing,
+// so every shared-memory access stays inside the warp's spans.
+template <typename KeyT, int WARPS, typename Sync>
+__device__ __forceinline__ void merge_partition_blocks(const KeyT* bufX, KeyT* bufY, const int* ctl,
+                                                       int* rows, KeyT* __restrict__ dstg, bool xout,
+                                                       int* dev_err, Sync sync) {
+  constexpr int E = Vec16<KeyT>::E;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nl = ctl[kCtlNodeFields * 32 + 0];       // levels of the tree over the runs (>= 1)
+  const int want = ctl[kCtlNodeFields * 32 + 2];     // items of the tile
+  const int nnodes = ctl[kCtlNodeFields * 32 + 1];
+  const int nleaf = 1 << nl;                         // segments, empty past the group's runs
+  // Segment r is child A (r even) or B (r odd) of level-1 node r / 2; the
+  // node table lists nodes in level order, so only its level-1 entries give
+  // segments (with 5 runs, say, nodes 0..2 are level 1 and segments 6, 7 are
+  // empty).
+  int seg_off = 0, seg_len = 0;
+  {
+    const int q = lane >> 1;
+    if (lane < nleaf && q < nnodes && ctl[7 * 32 + q] == 1) {
+      seg_off = ctl[(2 + (lane & 1)) * 32 + q];
+      seg_len = ctl[(lane & 1) * 32 + q];
+    }
+  }
+  const int nblk = (want + kBlockItems - 1) / kBlockItems;
+  if (warp == 0) {
+    rows[lane] = 0;
+    rows[nblk * 32 + lane] = seg_len;
+  } else if (warp < nblk) {
+    const int d = multiseq_pivot<KeyT, int>(bufX + seg_off, seg_len, lane < nleaf, nleaf,
+                                            warp * kBlockItems, 0xffffffffu);
+    rows[warp * 32 + lane] = d;
+  }
+  sync();
+  bool rows_ok = true;
+  if (warp < nblk) {
+    const int r0 = rows[warp * 32 + lane], r1 = rows[(warp + 1) * 32 + lane];
+    const int bm = (want - warp * kBlockItems) < kBlockItems ? (want - warp * kBlockItems) : kBlockItems;
+    const bool bad = lane < nleaf && (r0 < 0 || r1 < r0 || r1 > seg_len);
+    const int sum = (int)__reduce_add_sync(0xffffffffu, (lane < nleaf && !bad) ? (unsigned)(r1 - r0) : 0u);
+    rows_ok = !__any_sync(0xffffffffu, bad) && sum == bm;
+    if (!rows_ok && lane == 0) set_device_error(dev_err, kDevErrInternal);
+  }
+  if (warp < nblk && rows_ok) {
+    KeyT* blk = bufY + warp * kBlockItems;
+    const int r0 = rows[warp * 32 + lane];
+    int off = seg_off + r0;                          // lane q: sequence q of the level (bufX
+    int len = rows[(warp + 1) * 32 + lane] - r0;     // offsets at level 1, then blk offsets)
+    if (lane >= nleaf) len = 0;
+    for (int l = 1; l <= nl; ++l) {
+      const int npairs = nleaf >> l;
+      const int la = __shfl_sync(0xffffffffu, len, (2 * lane) & 31);
+      const int lb = __shfl_sync(0xffffffffu, len, (2 * lane + 1) & 31);
+      const int oa = __shfl_sync(0xffffffffu, off, (2 * lane) & 31);
+      const int ob = __shfl_sync(0xffffffffu, off, (2 * lane + 1) & 31);
+      const int olen = lane < npairs ? la + lb : 0;
+      int incl = olen;                               // outputs packed in pair order
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+      }
+      const int ooff = incl - olen;
+      const KeyT* src = (l == 1) ? bufX : blk;
+      const bool root = l == nl;
+      const bool xo = xout && root;
+      for (int p = 0; p < npairs; ++p) {
+        const int a = __shfl_sync(0xffffffffu, la, p);
+        const int b = __shfl_sync(0xffffffffu, lb, p);
+        const int m = a + b;
+        if (m == 0) continue;                        // uniform over the warp
+        const KeyT* A = src + __shfl_sync(0xffffffffu, oa, p);
+        const KeyT* B = src + __shfl_sync(0xffffffffu, ob, p);
+        KeyT* out = blk + __shfl_sync(0xffffffffu, ooff, p);
+        if (a == 0 || b == 0) {
+          // One side empty: a copy at the first level; later levels hold
+          // the items in place already (only the float transform remains).
+          if (l == 1 || xo) {
+            const KeyT* from = a ? A : B;
+            for (int i = lane; i < m; i += 32) {
+              const KeyT v = from[i];
+              out[i] = xo ? (KeyT)ordered_to_f32((uint32_t)v) : v;
+            }
+          }
+        } else if (root && m > kSmallBlockMax) {
+          if (l == 1)
+            warp_merge_block<KeyT, MergeMix, false>(A, a, B, b, out, lane, xo);
+          else
+            warp_merge_block<KeyT, MergeMix, true>(A, a, B, b, out, lane, xo);
+        } else {
+          warp_merge_any<KeyT>(A, a, B, b, out, lane, xo);
+        }
+        __syncwarp();
+      }
+      off = ooff;
+      len = olen;
+    }
+  }
+  const int body = (((uintptr_t)dstg & 15u) == 0) ? want / E * E : 0;   // off-grid: plain stores
+  fence_proxy_async_smem();
+  sync();
+  if (threadIdx.x == 0 && body > 0) bulk_s2g_and_wait(dstg, bufY, (unsigned)(body * sizeof(KeyT)));
+  for (int i = body + (int)threadIdx.x; i < want; i += WARPS * 32) dstg[i] = bufY[i];
+}
+
 // Merges output tile j (of S items, a multiple of 1024 and at most
 // 1024 * WARPS) of group g of `in` (n items in sorted runs of run_len, K runs
 // per group) into `out`: the CTA body of a merge round, one tile at a time.
@@ -361,7 +493,9 @@ __device__ __forceinline__ void merge_levels(KeyT* bufX, KeyT* bufY, const int* 
 // the staged data has arrived, thread 0 also waits on bar[1] for 16 bytes no
 // copy delivers, with a limit of about a millisecond, so the CTA takes the
 // time-out path with no copy in flight.
-template <typename KeyT, int WARPS>
+// PARTITION: merge with the heap-free variant above instead of the CTA tree
+// (shared memory of MergeGeom::bytes_partition).
+template <typename KeyT, int WARPS, bool PARTITION = false>
 __device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __restrict__ out,
                                            long long n, long long run_len, int K, long long g,
                                            long long j, const long long* __restrict__ lo_row,
@@ -399,8 +533,13 @@ __device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __
     if (threadIdx.x == 0) set_device_error(dev_err, kDevErrTimeout);
     return false;
   }
-  merge_levels<KeyT, WARPS>(bufX, bufY, ctl, out + g * run_len * K + j * S, xout,
-                            []() { __syncthreads(); });
+  if constexpr (PARTITION)
+    merge_partition_blocks<KeyT, WARPS>(bufX, bufY, ctl, ctl + kCtlNodeFields * 32 + kCtlScalars,
+                                        out + g * run_len * K + j * S, xout, dev_err,
+                                        []() { __syncthreads(); });
+  else
+    merge_levels<KeyT, WARPS>(bufX, bufY, ctl, out + g * run_len * K + j * S, xout,
+                              []() { __syncthreads(); });
   return true;
 }
 

@@ -484,11 +484,15 @@ __device__ __forceinline__ void warp_store_block(KeyT* out, int m, KeyT (&v)[32]
 // `out` is 16-byte aligned; the warp may use out[0, 32 * ceil((X + Y) / 32))
 // as transpose space, so up to 31 items past the block's end must be free.
 // M: the calling kernel's compare-exchange mix.
-template <typename KeyT, typename M>
+// INPLACE: `out` may overlap A and B (a merge of two adjacent sequences back
+// into their own span); the warp then synchronises between its loads and the
+// first store.
+template <typename KeyT, typename M, bool INPLACE = false>
 __device__ __forceinline__ void warp_merge_block(const KeyT* A, int X, const KeyT* B, int Y,
                                                  KeyT* out, int lane, bool xout) {
   KeyT v[32];
   warp_load_bitonic(A, X, B, Y, v, lane);
+  if constexpr (INPLACE) __syncwarp();
   warp_bitonic_1024<M>(v, out, (X + Y + 31) >> 5, lane);
   warp_store_block<KeyT>(out, X + Y, v, lane, xout);
 }
@@ -556,6 +560,20 @@ __device__ __forceinline__ void warp_merge_small(const KeyT* A, int X, const Key
   else if (m <= 64) warp_merge_small_r<2>(A, X, B, Y, out, lane, xout);
   else if (m <= 128) warp_merge_small_r<4>(A, X, B, Y, out, lane, xout);
   else warp_merge_small_r<8>(A, X, B, Y, out, lane, xout);
+}
+
+// Merges A[0, X) and B[0, Y) (X + Y <= 1024, any shared-memory offsets) into
+// out[0, X + Y) with the register-and-shuffle network of the smallest power
+// of two that holds them.  `out` may overlap A and B: every lane has loaded
+// all of its items before the first shuffle completes, and the stores follow
+// the shuffles.
+template <typename KeyT>
+__device__ __forceinline__ void warp_merge_any(const KeyT* A, int X, const KeyT* B, int Y,
+                                               KeyT* out, int lane, bool xout) {
+  const int m = X + Y;
+  if (m <= kSmallBlockMax) warp_merge_small<KeyT>(A, X, B, Y, out, lane, xout);
+  else if (m <= 512) warp_merge_small_r<16>(A, X, B, Y, out, lane, xout);
+  else warp_merge_small_r<32>(A, X, B, Y, out, lane, xout);
 }
 
 // ---------------------------------------------------------------------------

@@ -79,11 +79,14 @@ cudaError_t launch_splitter(int key_bytes, long long S, const void* in, long lon
 // items (a multiple of 1024, at most 1024 * tile_warps).  test_timeout: the
 // test hook of mms_options.test_flags (every CTA's extra wait runs out).
 // pdl: launch with programmatic stream serialization (the previous kernel on
-// the stream is one of this library's).
+// the stream is one of this library's).  partition: merge each tile with the
+// heap-free partition variant instead of the CTA merge tree (default tile
+// geometry only).
 cudaError_t launch_merge_pass(int key_bytes, int tile_warps, long long S, bool xout, const void* in,
                               void* out, long long n, long long run_len, int K,
                               const long long* table, int* dev_err, cudaStream_t s,
-                              bool test_timeout = false, bool pdl = false);
+                              bool test_timeout = false, bool pdl = false,
+                              bool partition = false);
 
 // Records the detail message mms_last_error_detail() returns on this thread.
 void set_error_detail(const char* msg);

@@ -123,27 +123,16 @@ __device__ __forceinline__ Item<KeyT> shfl_item(unsigned gm, const Item<KeyT>& i
   return o;
 }
 
-// Pivots of output tile j of group g, found by one lane group of W >= K lanes
-// (gm: its lanes, gb: its first lane; lane gb + r handles run r): row[r]
-// receives the number of items of run r among the group's first j * S
-// outputs.  Arguments are uniform over the lane group.  Idx is the type of
-// the counts and positions of the search: int when n < 2^30 (every position
-// probed stays below 2n), long long otherwise.
-template <typename KeyT, int W, typename Idx = long long>
-__device__ __forceinline__ void splitter_row(const KeyT* __restrict__ in, long long n,
-                                             long long run_len, int K, long long S, long long g,
-                                             long long j, long long* __restrict__ row,
-                                             unsigned gm, int gb) {
+// The search itself: the lanes of the group (lane gb + r on run r, act for
+// r < K) return the number of items each run contributes to the first k of
+// the K runs' merge under the order (key, run, position).  `run` and `rlen`
+// are the lane's run and its length (rlen = 0 when !act); the runs may lie in
+// global or in shared memory.  Arguments other than run / rlen / act are
+// uniform over the lane group; every lane of it must call.
+template <typename KeyT, typename Idx>
+__device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool act, int K, Idx k,
+                                              unsigned gm) {
   const int lane = threadIdx.x & 31;
-  const int rr = lane - gb;                     // run of this lane
-  const bool act = rr < K;
-  const long long rstart = g * run_len * K + (long long)rr * run_len;
-  long long rlen64 = n - rstart;
-  rlen64 = rlen64 < 0 ? 0 : (rlen64 > run_len ? run_len : rlen64);
-  const Idx rlen = act ? (Idx)rlen64 : Idx(0);
-  const KeyT* run = in + (act ? rstart : 0);
-  const Idx k = (Idx)(j * S);
-
   Idx d = 0;                  // selected samples of this run at the current stride
   Item<KeyT> e{KeyT(0), false};  // the d-th sample (position d*s-1) when d >= 1
   const int T = 64 - __clzll((long long)k);
@@ -198,6 +187,29 @@ __device__ __forceinline__ void splitter_row(const KeyT* __restrict__ in, long l
     d = cnt;
     e = top;
   }
+  return d;
+}
+
+// Pivots of output tile j of group g, found by one lane group of W >= K lanes
+// (gm: its lanes, gb: its first lane; lane gb + r handles run r): row[r]
+// receives the number of items of run r among the group's first j * S
+// outputs.  Arguments are uniform over the lane group.  Idx is the type of
+// the counts and positions of the search: int when n < 2^30 (every position
+// probed stays below 2n), long long otherwise.
+template <typename KeyT, int W, typename Idx = long long>
+__device__ __forceinline__ void splitter_row(const KeyT* __restrict__ in, long long n,
+                                             long long run_len, int K, long long S, long long g,
+                                             long long j, long long* __restrict__ row,
+                                             unsigned gm, int gb) {
+  const int lane = threadIdx.x & 31;
+  const int rr = lane - gb;                     // run of this lane
+  const bool act = rr < K;
+  const long long rstart = g * run_len * K + (long long)rr * run_len;
+  long long rlen64 = n - rstart;
+  rlen64 = rlen64 < 0 ? 0 : (rlen64 > run_len ? run_len : rlen64);
+  const Idx rlen = act ? (Idx)rlen64 : Idx(0);
+  const KeyT* run = in + (act ? rstart : 0);
+  const Idx d = multiseq_pivot<KeyT, Idx>(run, rlen, act, K, (Idx)(j * S), gm);
   if (act) row[rr] = d;
 }
 
