@@ -10,7 +10,7 @@ size_t merge_pass_smem_bytes(int key_bytes, int warps, int K) {
 }
 
 template <typename KeyT, int WARPS, bool XOUT, bool PART>
-__global__ void __launch_bounds__(WARPS * 32, (MinBlocks<KeyT, WARPS>::value))
+__global__ void __launch_bounds__(WARPS * 32, (PART ? kPartitionMinBlocks : MinBlocks<KeyT, WARPS>::value))
     merge_pass_kernel(const KeyT* __restrict__ in, KeyT* __restrict__ out, long long n,
                       long long run_len, int K, const long long* __restrict__ table,
                       long long tpg, int S, int* dev_err, int test_timeout) {

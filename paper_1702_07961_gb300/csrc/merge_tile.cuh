@@ -404,8 +404,18 @@ __device__ __forceinline__ void merge_partition_blocks(const KeyT* bufX, KeyT* b
     rows[lane] = 0;
     rows[nblk * 32 + lane] = seg_len;
   } else if (warp < nblk) {
-    const int d = multiseq_pivot<KeyT, int>(bufX + seg_off, seg_len, lane < nleaf, nleaf,
-                                            warp * kBlockItems, 0xffffffffu);
+    const int k = warp * kBlockItems;
+    int d;
+    if (nleaf == 2) {
+      // Two segments: the search is the merge-path co-rank (ties from the
+      // lower run, as in the order of Sec. 4.1).
+      const int o0 = __shfl_sync(0xffffffffu, seg_off, 0), l0 = __shfl_sync(0xffffffffu, seg_len, 0);
+      const int o1 = __shfl_sync(0xffffffffu, seg_off, 1), l1 = __shfl_sync(0xffffffffu, seg_len, 1);
+      const int a = warp_corank(bufX + o0, l0, bufX + o1, l1, k, lane);
+      d = lane == 0 ? a : (lane == 1 ? k - a : 0);
+    } else {
+      d = multiseq_pivot<KeyT, int>(bufX + seg_off, seg_len, lane < nleaf, nleaf, k, 0xffffffffu);
+    }
     rows[warp * 32 + lane] = d;
   }
   sync();

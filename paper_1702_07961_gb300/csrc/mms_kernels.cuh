@@ -32,6 +32,12 @@ struct MinBlocks {
   static constexpr int value = 3;
 };
 
+// CTAs per SM the partition variant of the merge pass is compiled for: two
+// (128 registers, no spills) measured faster on GB300 than three (80
+// registers, about 650 bytes of spills): 10^8 u32 keys 18.4 against 14.7
+// Gkeys/s.
+constexpr int kPartitionMinBlocks = 2;
+
 // Items of slack past a tile buffer: a partial block's transpose may use up
 // to 31 items past the block's end.
 constexpr int kTileSlack = 32;
