@@ -124,11 +124,22 @@ __device__ __forceinline__ void cas_dir(uint64_t& a, uint64_t& b, bool flip) {
 // and 12 of 16 direction pairs, the merge pass (barrier-bound, ALU 57%) with
 // plain pairs as min/max and 12 of 16 direction pairs; each kernel passes its
 // own Mix type.  The multiply-adds use a runtime 1 (and -1, -2) so that the
-// compiler keeps them multiplies.  64-bit keys take min/max only.
+// compiler keeps them multiplies.
+//
+// 64-bit keys: a compare-exchange is one 64-bit compare and four 32-bit
+// selects on the ALU pipe.  The selects can also be made exact multiply-adds
+// on the FMA pipe: with f = 1 when the pair swaps, each half x of a and y of
+// b becomes x + f (y - x) and y + f (x - y).  That form costs more issue
+// slots, so it pays only where the ALU pipe is the tighter limit: measured on
+// GB300 at 10^8 u64 keys, 6 of 16 plain pairs of the merge pass in it took the
+// five K = 8 passes from 4.686 to 4.594 ms, while any share of the base
+// case's pairs, or of direction pairs, made it slower (base case 1.85 ->
+// 2.00..2.30 ms).
 // ---------------------------------------------------------------------------
 // MIX / MIXD: how many of a stage's 16 pairs take the multiply-add form, for
-// plain pairs and for pairs whose direction is chosen per lane.
-template <int MIX, int MIXD>
+// plain pairs and for pairs whose direction is chosen per lane, with 32-bit
+// keys; MIX64 / MIXD64 the same with 64-bit keys.
+template <int MIX, int MIXD, int MIX64, int MIXD64>
 struct Mix {
   uint32_t one, m1, m2;   // 1, -1, -2 (mod 2^32), unknown to the compiler
 };
@@ -156,8 +167,9 @@ __device__ __forceinline__ constexpr int pair_ordinal(int k, int s) {
 }
 
 // Compare-exchange (ascending) of a stage pair with ordinal i.
-template <int MIX, int MIXD>
-__device__ __forceinline__ void cas_mix(uint32_t& a, uint32_t& b, int i, const Mix<MIX, MIXD>& c) {
+template <int MIX, int MIXD, int MIX64, int MIXD64>
+__device__ __forceinline__ void cas_mix(uint32_t& a, uint32_t& b, int i,
+                                        const Mix<MIX, MIXD, MIX64, MIXD64>& c) {
   if (mad_pick(i, MIX)) {
     const uint32_t lo = min(a, b);
     const uint32_t s = mad_u32(a, c.one, b);
@@ -167,15 +179,35 @@ __device__ __forceinline__ void cas_mix(uint32_t& a, uint32_t& b, int i, const M
     cas(a, b);
   }
 }
-template <int MIX, int MIXD>
-__device__ __forceinline__ void cas_mix(uint64_t& a, uint64_t& b, int, const Mix<MIX, MIXD>&) {
-  cas(a, b);
+
+// 64-bit pair: swap when sw, the selects as multiply-adds (exact for f in
+// {0, 1}).
+template <typename M>
+__device__ __forceinline__ void swap64_mad(uint64_t& a, uint64_t& b, bool sw, const M& c) {
+  const uint32_t f = sw ? c.one : 0u;
+  const uint32_t al = (uint32_t)a, ah = (uint32_t)(a >> 32);
+  const uint32_t bl = (uint32_t)b, bh = (uint32_t)(b >> 32);
+  const uint32_t dl = mad_u32(al, c.m1, bl), el = mad_u32(bl, c.m1, al);   // bl - al, al - bl
+  const uint32_t dh = mad_u32(ah, c.m1, bh), eh = mad_u32(bh, c.m1, ah);
+  const uint32_t xl = mad_u32(f, dl, al), yl = mad_u32(f, el, bl);         // sw ? b : a, sw ? a : b
+  const uint32_t xh = mad_u32(f, dh, ah), yh = mad_u32(f, eh, bh);
+  a = ((uint64_t)xh << 32) | xl;
+  b = ((uint64_t)yh << 32) | yl;
+}
+
+template <int MIX, int MIXD, int MIX64, int MIXD64>
+__device__ __forceinline__ void cas_mix(uint64_t& a, uint64_t& b, int i,
+                                        const Mix<MIX, MIXD, MIX64, MIXD64>& c) {
+  if (mad_pick(i, MIX64))
+    swap64_mad(a, b, b < a, c);
+  else
+    cas(a, b);
 }
 
 // cas_dir with the direction as f in {0, 1} (1: the larger key goes to a).
-template <int MIX, int MIXD>
+template <int MIX, int MIXD, int MIX64, int MIXD64>
 __device__ __forceinline__ void cas_dir_mix(uint32_t& a, uint32_t& b, uint32_t f, int i,
-                                            const Mix<MIX, MIXD>& c) {
+                                            const Mix<MIX, MIXD, MIX64, MIXD64>& c) {
   if (mad_pick(i, MIXD)) {
     const uint32_t lo = min(a, b);
     const uint32_t s = mad_u32(a, c.one, b);   // a + b
@@ -187,15 +219,19 @@ __device__ __forceinline__ void cas_dir_mix(uint32_t& a, uint32_t& b, uint32_t f
     cas_dir(a, b, f != 0);
   }
 }
-template <int MIX, int MIXD>
-__device__ __forceinline__ void cas_dir_mix(uint64_t& a, uint64_t& b, uint32_t f, int,
-                                            const Mix<MIX, MIXD>&) {
-  cas_dir(a, b, f != 0);
+template <int MIX, int MIXD, int MIX64, int MIXD64>
+__device__ __forceinline__ void cas_dir_mix(uint64_t& a, uint64_t& b, uint32_t f, int i,
+                                            const Mix<MIX, MIXD, MIX64, MIXD64>& c) {
+  if (mad_pick(i, MIXD64))
+    swap64_mad(a, b, (b < a) != (f != 0), c);
+  else
+    cas_dir(a, b, f != 0);
 }
 
-// The mixes the kernels use (multiply-add pairs of 16: plain, per-lane direction).
-using TileMix = Mix<kTileMadPairs, kTileMadDirPairs>;
-using MergeMix = Mix<kMergeMadPairs, kMergeMadDirPairs>;
+// The mixes the kernels use (multiply-add pairs of 16: plain and per-lane
+// direction, 32-bit keys then 64-bit keys).
+using TileMix = Mix<kTileMadPairs, kTileMadDirPairs, kTileMad64Pairs, kTileMad64DirPairs>;
+using MergeMix = Mix<kMergeMadPairs, kMergeMadDirPairs, kMergeMad64Pairs, kMergeMad64DirPairs>;
 
 
 // ---------------------------------------------------------------------------

@@ -18,6 +18,9 @@ constexpr int kMaxFanout = 32;
 // case and the merge pass (plain pairs, pairs with a per-lane direction).
 constexpr int kTileMadPairs = 6, kTileMadDirPairs = 12;
 constexpr int kMergeMadPairs = 0, kMergeMadDirPairs = 12;
+// The same for 64-bit keys (their selects as multiply-adds; see mms_common.cuh).
+constexpr int kTileMad64Pairs = 0, kTileMad64DirPairs = 0;
+constexpr int kMergeMad64Pairs = 6, kMergeMad64DirPairs = 0;
 
 // Device error word values (the first word of a sort workspace).
 constexpr int kDevOk = 0;
