@@ -53,6 +53,8 @@ def parse():
                    help="sort workload: a uniform permutation (the headline), a sortedness input with "
                         "--swaps pair swaps, or --runs runs interleaved at --stride")
     p.add_argument("--swaps", type=int, default=0)
+    p.add_argument("--seed", type=int, default=1,
+                   help="seed of the synthetic input (rank r of a replica run uses seed + r)")
     p.add_argument("--runs", type=int, default=8)
     p.add_argument("--stride", type=int, default=32)
     p.add_argument("--min-timed-s", type=float, default=1.0,
@@ -274,16 +276,17 @@ def make_sort_input(args, N: int, rank: int):
     import numpy as np
     import synth
     if args.key == "f32":
-        return synth.normal_f32(N, 3 + rank), "N(0,1) float32 with 1% duplicates, 0.1% -0.0, 0.01% NaN"
+        return (synth.normal_f32(N, args.seed + 2 + rank),
+                "N(0,1) float32 with 1% duplicates, 0.1% -0.0, 0.01% NaN")
     if args.input == "sortedness":
-        v = synth.sortedness_cached(N, args.swaps, 2 + rank) if args.swaps >= 10**6 else \
-            synth.sortedness(N, args.swaps, 2 + rank)
+        v = synth.sortedness_cached(N, args.swaps, args.seed + 1 + rank) if args.swaps >= 10**6 else \
+            synth.sortedness(N, args.swaps, args.seed + 1 + rank)
         desc = f"sortedness: 0..N-1 then {args.swaps} random pair swaps (Sec. 1)"
     elif args.input == "interleaved":
         v = synth.interleaved(N, args.runs, args.stride)
         desc = f"{args.runs} sorted runs interleaved at stride {args.stride} (C3 layout)"
     else:
-        v = synth.permutation(N, 1 + rank)
+        v = synth.permutation(N, args.seed + rank)
         desc = "uniform random permutation of 0..N-1 (Sec. 6.3 'fully random')"
     if args.key == "u64":
         w = v.astype(np.uint64)
@@ -954,12 +957,14 @@ def main():
                                + ", one sort per step",
                    "global_batch": N * world, "seq_len": None, "parallelism": f"replicas{world}",
                    "plan_fanouts": plan, "tile": args.tile or mms.tile_items(kt),
-                   "merge_variant": args.merge_variant,
+                   "merge_variant": args.merge_variant, "seed": args.seed + rank,
                    "l2": f"input {N * kb / 1e6:.0f} MB > 129 MB L2; a device copy restores the input "
                          "before every step, outside the timed events" if N * kb > 129e6 else
                          "input fits in L2"},
         "timed_windows": {"count": len(windows), "steps_each": args.steps,
                           "gkeys_per_s": [w[1] for w in windows],
+                          "mean": statistics.mean(w[1] for w in windows),
+                          "min": min(w[1] for w in windows), "max": max(w[1] for w in windows),
                           "note": "value and ms_per_step are the median window's"},
         "stages_ms": {"tile_sort": tile_ms, "splitter": split_ms, "merge_pass": merge_ms,
                       "pairs_finalize": gather_ms, "dominant": dominant,
