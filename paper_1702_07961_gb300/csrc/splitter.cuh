@@ -106,6 +106,20 @@ __device__ __forceinline__ int grp_argmax(unsigned gm, bool cond, const Item<Key
   }
 }
 
+// grp_argmax when no lane of the group holds a pad: one max and one ballot
+// (4-byte keys), or the two-word maximum (8-byte keys).
+template <typename KeyT>
+__device__ __forceinline__ int grp_argmax_real(unsigned gm, bool cond, KeyT key) {
+  if constexpr (sizeof(KeyT) == 4) {
+    const uint32_t mx = grp_max_u32(gm, cond ? (uint32_t)key : 0u);
+    const unsigned m = __ballot_sync(gm, cond && (uint32_t)key == mx);
+    return m ? 31 - __clz(m) : -1;
+  } else {
+    if (!__ballot_sync(gm, cond)) return -1;
+    return 31 - __clz(lanes_with_max(gm, cond, key));
+  }
+}
+
 template <typename KeyT>
 __device__ __forceinline__ int grp_argmin(unsigned gm, bool cond, const Item<KeyT>& it) {
   const unsigned any = __ballot_sync(gm, cond);
@@ -143,6 +157,9 @@ __device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool ac
     Item<KeyT> o = load_item(run, rlen, ((dd + 1) << sh) - 1);
     Item<KeyT> z{KeyT(0), false};
     if (d >= 1) z = load_item(run, rlen, ((dd - 1) << sh) - 1);
+    // Pads at this level: o is a lane's highest position, so when no o is a
+    // pad, no item of the level is (e, z and any deeper item lie below o).
+    const bool any_pad = __any_sync(gm, act && o.pad);
     // Items to drop: (sum of the lanes' 2d + 1) - kp, which lies in [0, K];
     // one 32-bit warp reduction, exact modulo 2^32 since the result is small.
     const unsigned dsum = __reduce_add_sync(gm, act ? (unsigned)d : 0u);
@@ -151,7 +168,7 @@ __device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool ac
 
     // Candidates above every selected item are dropped first, in one step.
     const bool hasZ = act && d >= 1;
-    const int mz = grp_argmax(gm, hasZ, e);
+    const int mz = any_pad ? grp_argmax(gm, hasZ, e) : grp_argmax_real(gm, hasZ, e.key);
     bool above = act;
     if (mz >= 0) {
       const Item<KeyT> zmax = shfl_item(gm, e, mz);
@@ -171,7 +188,8 @@ __device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool ac
     // Remaining drops one at a time from the largest current top.
     Item<KeyT> top = (cnt == dd + 1) ? o : e;
     for (Idx p = 0; p < pops; ++p) {
-      const int w = grp_argmax(gm, act && cnt >= 1, top);
+      const int w = any_pad ? grp_argmax(gm, act && cnt >= 1, top)
+                            : grp_argmax_real(gm, act && cnt >= 1, top.key);
       if (lane == w) {
         cnt -= 1;
         if (cnt >= 1) {
