@@ -160,10 +160,10 @@ __device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool ac
     // Pads at this level: o is a lane's highest position, so when no o is a
     // pad, no item of the level is (e, z and any deeper item lie below o).
     const bool any_pad = __any_sync(gm, act && o.pad);
-    // Items to drop: (sum of the lanes' 2d + 1) - kp, which lies in [0, K];
-    // one 32-bit warp reduction, exact modulo 2^32 since the result is small.
-    const unsigned dsum = __reduce_add_sync(gm, act ? (unsigned)d : 0u);
-    const Idx jrem = (int)(2u * dsum + (unsigned)K - (unsigned)kp);
+    // Items to drop: (sum of the lanes' 2d + 1) - kp.  The lanes hold the
+    // pivots of rank k >> lev, so the d sum to k >> (sh + 1) and the count is
+    // K minus the low bit of kp: K - 1 or K, with no reduction.
+    const Idx jrem = (Idx)K - (kp & 1);
     Idx cnt = dd + 1;
 
     // Candidates above every selected item are dropped first, in one step.
@@ -171,8 +171,13 @@ __device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool ac
     const int mz = any_pad ? grp_argmax(gm, hasZ, e) : grp_argmax_real(gm, hasZ, e.key);
     bool above = act;
     if (mz >= 0) {
-      const Item<KeyT> zmax = shfl_item(gm, e, mz);
-      above = act && (lane == mz || before_cross(zmax, mz, o, lane));
+      if (any_pad) {
+        const Item<KeyT> zmax = shfl_item(gm, e, mz);
+        above = act && (lane == mz || before_cross(zmax, mz, o, lane));
+      } else {                                  // no pads: keys, then runs
+        const KeyT zk = __shfl_sync(gm, e.key, mz);
+        above = act && (lane == mz || zk < o.key || (zk == o.key && mz < lane));
+      }
     }
     const unsigned abovem = __ballot_sync(gm, above);
     const Idx u = __popc(abovem);

@@ -10,8 +10,8 @@ floor(2k/s).  The model replays those steps one lane per run -- the same
 probes, the same "drop every candidate above all selected items first" step,
 the same pops from the largest top -- and checks:
   * the result equals brute force on small inputs with many duplicates;
-  * every level drops K - 1 or K items, the range that lets the kernel count
-    them with one 32-bit warp reduction modulo 2^32;
+  * every level drops K - 1 or K items: K minus the low bit of the level's
+    rank, the closed form the kernel uses instead of a reduction;
   * every probed position lies below 2k, so for n < 2^30 the kernel's 32-bit
     counts and positions cannot overflow.
 """
@@ -68,6 +68,8 @@ def splitter_model(runs, k, drops):
         o = [item(runs[r], ((dd[r] + 1) << sh) - 1) for r in range(K)]
         z = [item(runs[r], ((dd[r] - 1) << sh) - 1) if d[r] >= 1 else (False, 0) for r in range(K)]
         jrem = 2 * sum(d) + K - kp
+        # the kernel's closed form: the lanes hold the pivots of rank k >> lev, so sum(d) = k >> lev
+        assert sum(d) == k >> lev and jrem == K - (kp & 1)
         drops.append((jrem, K))
         cnt = [x + 1 for x in dd]
         mz = argmax([r for r in range(K) if d[r] >= 1], e)
