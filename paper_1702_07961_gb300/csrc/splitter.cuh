@@ -190,8 +190,17 @@ __device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool ac
       if (above && lane != mn) cnt = dd;
       pops = 0;
     }
-    // Remaining drops one at a time from the largest current top.
+    // Remaining drops one at a time from the largest current top.  The first
+    // needs no reduction: the largest top is lane mz's e (every candidate
+    // above it was dropped, mz's own included), and mz then falls back to z.
     Item<KeyT> top = (cnt == dd + 1) ? o : e;
+    if (mz >= 0 && pops > 0) {                  // uniform over the group
+      if (lane == mz) {
+        cnt = dd - 1;                           // d >= 1 on lane mz, so cnt >= 1
+        top = z;
+      }
+      pops -= 1;
+    }
     for (Idx p = 0; p < pops; ++p) {
       const int w = any_pad ? grp_argmax(gm, act && cnt >= 1, top)
                             : grp_argmax_real(gm, act && cnt >= 1, top.key);

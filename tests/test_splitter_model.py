@@ -87,6 +87,13 @@ def splitter_model(runs, k, drops):
                     cnt[r] = dd[r]
             pops = 0
         top = [o[r] if cnt[r] == dd[r] + 1 else e[r] for r in range(K)]
+        if mz >= 0 and pops > 0:
+            # the kernel's first drop without a reduction: the largest top is
+            # lane mz's e, whose own candidate the bulk step dropped
+            assert argmax([r for r in range(K) if cnt[r] >= 1], top) == mz and cnt[mz] == dd[mz]
+            cnt[mz] -= 1
+            top[mz] = z[mz]
+            pops -= 1
         for _ in range(pops):
             w = argmax([r for r in range(K) if cnt[r] >= 1], top)
             cnt[w] -= 1
