@@ -201,9 +201,7 @@ __device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool ac
       }
       pops -= 1;
     }
-    for (Idx p = 0; p < pops; ++p) {
-      const int w = any_pad ? grp_argmax(gm, act && cnt >= 1, top)
-                            : grp_argmax_real(gm, act && cnt >= 1, top.key);
+    auto drop = [&](int w) {
       if (lane == w) {
         cnt -= 1;
         if (cnt >= 1) {
@@ -215,6 +213,11 @@ __device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool ac
             top = load_item(run, rlen, (cnt << sh) - 1);
         }
       }
+    };
+    if (any_pad) {
+      for (Idx p = 0; p < pops; ++p) drop(grp_argmax(gm, act && cnt >= 1, top));
+    } else {
+      for (Idx p = 0; p < pops; ++p) drop(grp_argmax_real(gm, act && cnt >= 1, top.key));
     }
     d = cnt;
     e = top;
