@@ -143,7 +143,10 @@ __device__ __forceinline__ Item<KeyT> shfl_item(unsigned gm, const Item<KeyT>& i
 // are the lane's run and its length (rlen = 0 when !act); the runs may lie in
 // global or in shared memory.  Arguments other than run / rlen / act are
 // uniform over the lane group; every lane of it must call.
-template <typename KeyT, typename Idx>
+// UNSWITCH: one drop loop per arg-max form (no pad test inside the loop);
+// measured faster in the splitter kernel (splitter_row), slower inside the
+// much larger partition merge kernel, which takes the default single loop.
+template <typename KeyT, typename Idx, bool UNSWITCH = false>
 __device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool act, int K, Idx k,
                                               unsigned gm) {
   const int lane = threadIdx.x & 31;
@@ -214,10 +217,16 @@ __device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool ac
         }
       }
     };
-    if (any_pad) {
-      for (Idx p = 0; p < pops; ++p) drop(grp_argmax(gm, act && cnt >= 1, top));
+    if constexpr (UNSWITCH) {
+      if (any_pad) {
+        for (Idx p = 0; p < pops; ++p) drop(grp_argmax(gm, act && cnt >= 1, top));
+      } else {
+        for (Idx p = 0; p < pops; ++p) drop(grp_argmax_real(gm, act && cnt >= 1, top.key));
+      }
     } else {
-      for (Idx p = 0; p < pops; ++p) drop(grp_argmax_real(gm, act && cnt >= 1, top.key));
+      for (Idx p = 0; p < pops; ++p)
+        drop(any_pad ? grp_argmax(gm, act && cnt >= 1, top)
+                     : grp_argmax_real(gm, act && cnt >= 1, top.key));
     }
     d = cnt;
     e = top;
@@ -244,7 +253,7 @@ __device__ __forceinline__ void splitter_row(const KeyT* __restrict__ in, long l
   rlen64 = rlen64 < 0 ? 0 : (rlen64 > run_len ? run_len : rlen64);
   const Idx rlen = act ? (Idx)rlen64 : Idx(0);
   const KeyT* run = in + (act ? rstart : 0);
-  const Idx d = multiseq_pivot<KeyT, Idx>(run, rlen, act, K, (Idx)(j * S), gm);
+  const Idx d = multiseq_pivot<KeyT, Idx, true>(run, rlen, act, K, (Idx)(j * S), gm);
   if (act) row[rr] = d;
 }
 
