@@ -45,8 +45,9 @@ def parse():
     p.add_argument("--fanout", type=int, default=0, help="merge fanout K (0 = planner)")
     p.add_argument("--tile", type=int, default=0, help="tile items (0 = library default)")
     p.add_argument("--pairs", action="store_true", help="key + uint32 index payload (stable key-value sort)")
-    p.add_argument("--merge-variant", default="tree", choices=["tree", "partition"],
-                   help="merge rounds: the CTA merge tree (default) or the heap-free partition variant")
+    p.add_argument("--merge-variant", default="tree", choices=["tree", "partition", "pipelined"],
+                   help="merge rounds: the CTA merge tree (default), the heap-free partition variant or "
+                        "the pipelined variant")
     p.add_argument("--key", default="u32", choices=["u32", "u64", "f32"],
                    help="sort workload: key type (the headline is u32)")
     p.add_argument("--input", default="permutation", choices=["permutation", "sortedness", "interleaved"],
@@ -832,7 +833,8 @@ def main():
     plan = mms.plan(kt, N, args.fanout, args.tile, pairs=args.pairs)
     n_ev = 2 + 2 * len(plan) + (1 if args.pairs else 0)
     stream = torch.cuda.current_stream()
-    mv = mms.MERGE_PARTITION if args.merge_variant == "partition" else mms.MERGE_TREE
+    mv = {"partition": mms.MERGE_PARTITION, "pipelined": mms.MERGE_PIPELINED}.get(args.merge_variant,
+                                                                                  mms.MERGE_TREE)
 
     def step(events=None, bounds=None):
         work.copy_(src)
@@ -933,7 +935,7 @@ def main():
         achieved = bytes_pass / (tile_ms / 1e3) / 1e9
     headline = (args.key == "u32" and not args.pairs and args.input == "permutation"
                 and args.merge_variant == "tree")
-    partition_run = args.merge_variant == "partition" and args.key == "u32" and not args.pairs
+    partition_run = args.merge_variant != "tree" and args.key == "u32" and not args.pairs
     traffic = load_traffic(N, "merge_pass_kernel") if headline and merge_avg else None
     roofline = {"bound": "hbm", "kernel": "merge_pass" if merge_avg else "tile_sort",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -948,7 +950,7 @@ def main():
 
     out = {
         "metric": METRIC if headline else (f"Gkeys/s at {N} {args.key}" + (" pairs" if args.pairs else "")
-                                           + (" (partition merge)" if args.merge_variant == "partition" else "")),
+                                           + (f" ({args.merge_variant} merge)" if args.merge_variant != "tree" else "")),
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.key, "data": "synthetic",

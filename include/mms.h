@@ -80,14 +80,18 @@ typedef struct {
                         MMS_MERGE_PARTITION: the heap-free variant of Sec. 7 (future
                         work), each warp finding its 1024-key output block's pieces in
                         the tile's K segments by the partitioning search of Sec. 4.1 and
-                        merging them alone.  Same results; the partition variant takes
-                        the default tile geometry only (tile_items and merge_tile_items
-                        0) and applies to mms_sort_keys_ex and mms_sort_pairs_ex. */
+                        merging them alone; MMS_MERGE_PIPELINED: the pipelining of
+                        Sec. 7 (future work), persistent CTAs whose producer warp plans
+                        and stages the next tile while the merging warps merge the
+                        current one.  Same results; the variants take the default tile
+                        geometry only (tile_items and merge_tile_items 0), apply to
+                        mms_sort_keys_ex and mms_sort_pairs_ex, and take no test flags. */
 } mms_options;
 
 #define MMS_TEST_STAGING_TIMEOUT 1
 #define MMS_MERGE_TREE 0
 #define MMS_MERGE_PARTITION 1
+#define MMS_MERGE_PIPELINED 2
 
 /* Bytes of workspace mms_sort_keys / mms_sort_pairs need for n keys: one
  * ping-pong copy of the keys (and values), the pivot table of the largest
@@ -180,6 +184,16 @@ mms_status mms_merge_pass(mms_key_type kt, const void* d_in, void* d_out, size_t
  * merges its own pieces.  Arguments, layout, ownership and errors as for
  * mms_merge_pass; the output is identical. */
 mms_status mms_merge_pass_partition(mms_key_type kt, const void* d_in, void* d_out, size_t n,
+                                    size_t run_len, int K, const int64_t* d_table, void* d_ws,
+                                    size_t ws_bytes, void* stream);
+
+/* The same round merged by the pipelined variant (Sec. 7, future work;
+ * mms_options.merge_variant = MMS_MERGE_PIPELINED): persistent CTAs, each
+ * with a producer warp that plans and stages tile q + 1 into the third of
+ * three tile buffers while its merging warps merge tile q.  Arguments,
+ * layout, ownership and errors as for mms_merge_pass; the output is
+ * identical. */
+mms_status mms_merge_pass_pipelined(mms_key_type kt, const void* d_in, void* d_out, size_t n,
                                     size_t run_len, int K, const int64_t* d_table, void* d_ws,
                                     size_t ws_bytes, void* stream);
 

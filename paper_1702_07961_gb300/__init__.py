@@ -48,10 +48,12 @@ class _Options(ctypes.Structure):
 # bounded wait run out (MMS_TEST_STAGING_TIMEOUT).
 TEST_STAGING_TIMEOUT = 1
 
-# mms_options.merge_variant: the CTA merge tree (default) or the heap-free
-# partition variant (MMS_MERGE_TREE, MMS_MERGE_PARTITION).
+# mms_options.merge_variant: the CTA merge tree (default), the heap-free
+# partition variant or the pipelined variant (MMS_MERGE_TREE,
+# MMS_MERGE_PARTITION, MMS_MERGE_PIPELINED).
 MERGE_TREE = 0
 MERGE_PARTITION = 1
+MERGE_PIPELINED = 2
 
 
 class _SegOptions(ctypes.Structure):
@@ -101,6 +103,8 @@ def load() -> ctypes.CDLL:
         L.mms_merge_pass.restype = i32
         L.mms_merge_pass_partition.argtypes = [i32, vp, vp, sz, sz, i32, vp, vp, sz, vp]
         L.mms_merge_pass_partition.restype = i32
+        L.mms_merge_pass_pipelined.argtypes = [i32, vp, vp, sz, sz, i32, vp, vp, sz, vp]
+        L.mms_merge_pass_pipelined.restype = i32
         L.mms_sort_keys_noalloc.argtypes = [i32, vp, sz, vp]
         L.mms_sort_keys_noalloc.restype = i32
         L.mms_segmented_workspace_bytes.argtypes = [i32, sz, sz, i32, ctypes.POINTER(_SegOptions)]
@@ -199,7 +203,7 @@ def sort_keys(keys, fanout: int = 0, workspace=None, stream=None, kt: int | None
     ``events``: optional list of ``torch.cuda.Event(enable_timing=True)``; the
     library records them before the first kernel and after each kernel.
     ``test_flags``: test hooks (``TEST_STAGING_TIMEOUT``), 0 in normal use.
-    ``merge_variant``: ``MERGE_TREE`` or ``MERGE_PARTITION``.
+    ``merge_variant``: ``MERGE_TREE``, ``MERGE_PARTITION`` or ``MERGE_PIPELINED``.
     """
     assert keys.is_cuda and keys.is_contiguous()
     kt = key_type_of(keys) if kt is None else kt
@@ -261,10 +265,13 @@ def splitter(data, run_len: int, K: int, table=None, stream=None, kt: int | None
 def merge_pass(inp, out, run_len: int, K: int, table, workspace=None, stream=None, kt: int | None = None,
                merge_variant: int = MERGE_TREE):
     """One K-way merge round of ``inp`` into ``out`` driven by ``table``
-    (``mms_merge_pass``, or ``mms_merge_pass_partition`` for MERGE_PARTITION)."""
+    (``mms_merge_pass``; ``mms_merge_pass_partition`` / ``mms_merge_pass_pipelined``
+    for MERGE_PARTITION / MERGE_PIPELINED)."""
     kt = key_type_of(inp) if kt is None else kt
     ws_ptr, ws_len = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
-    fn = load().mms_merge_pass_partition if merge_variant == MERGE_PARTITION else load().mms_merge_pass
+    L = load()
+    fn = {MERGE_PARTITION: L.mms_merge_pass_partition,
+          MERGE_PIPELINED: L.mms_merge_pass_pipelined}.get(merge_variant, L.mms_merge_pass)
     _check(fn(kt, _ptr(inp), _ptr(out), inp.numel(), run_len, K, _ptr(table),
               ws_ptr, ws_len, _stream_handle(stream)))
     return out

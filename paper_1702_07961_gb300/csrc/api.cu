@@ -11,6 +11,7 @@
 
 #include "../../include/mms.h"
 #include "mms_kernels.cuh"
+#include "merge_pipelined.cuh"
 
 namespace {
 
@@ -317,11 +318,13 @@ mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws,
       (opt->merge_tile_items % 1024 != 0 || opt->merge_tile_items < (kb == 8 ? 2048 : 4096) ||
        opt->merge_tile_items > S))
     return fail(MMS_ERR_INVALID_ARG, "merge_tile_items must be 0 or a multiple of 1024 from the smallest tile up to tile_items%s");
-  if (opt && opt->merge_variant != MMS_MERGE_TREE && opt->merge_variant != MMS_MERGE_PARTITION)
-    return fail(MMS_ERR_INVALID_ARG, "merge_variant must be MMS_MERGE_TREE or MMS_MERGE_PARTITION%s");
-  const bool partition = opt && opt->merge_variant == MMS_MERGE_PARTITION;
-  if (partition && (opt->tile_items != 0 || opt->merge_tile_items != 0))
-    return fail(MMS_ERR_INVALID_ARG, "the partition merge variant takes the default tile geometry (tile_items and merge_tile_items 0)%s");
+  const int variant = opt ? opt->merge_variant : MMS_MERGE_TREE;
+  if (variant != MMS_MERGE_TREE && variant != MMS_MERGE_PARTITION && variant != MMS_MERGE_PIPELINED)
+    return fail(MMS_ERR_INVALID_ARG, "merge_variant must be MMS_MERGE_TREE, MMS_MERGE_PARTITION or MMS_MERGE_PIPELINED%s");
+  const bool partition = variant == MMS_MERGE_PARTITION;
+  const bool pipelined = variant == MMS_MERGE_PIPELINED;
+  if ((partition || pipelined) && (opt->tile_items != 0 || opt->merge_tile_items != 0 || opt->test_flags != 0))
+    return fail(MMS_ERR_INVALID_ARG, "the partition and pipelined merge variants take the default tile geometry (tile_items and merge_tile_items 0) and no test flags%s");
   const WsLayout L = ws_layout(kt, n, 0);
   cudaStream_t s = (cudaStream_t)stream;
   bool owned = false;
@@ -365,9 +368,13 @@ mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws,
                       "splitter");
     mark();
     if (st != MMS_OK) break;
-    st = check_launch(mms::launch_merge_pass(kb, tw, Sm, is_f32 && r == rounds - 1, cur, other,
-                                             (long long)n, run_len, K[r], table, dev_err, s,
-                                             test_timeout, true, partition),
+    st = check_launch(pipelined
+                          ? mms::launch_merge_pipelined(kb, is_f32 && r == rounds - 1, cur, other,
+                                                        (long long)n, run_len, K[r], table, dev_err,
+                                                        s, true)
+                          : mms::launch_merge_pass(kb, tw, Sm, is_f32 && r == rounds - 1, cur, other,
+                                                   (long long)n, run_len, K[r], table, dev_err, s,
+                                                   test_timeout, true, partition),
                       "merge_pass");
     mark();
     void* t = cur;
@@ -424,9 +431,14 @@ static mms_status pairs32_run(bool is_f32, void* d_keys, uint32_t* d_values, siz
                       "splitter");
     mark();
     if (st != MMS_OK) break;
-    st = check_launch(mms::launch_merge_pass(8, tw, S, false, comp[cur], comp[1 - cur], (long long)n,
-                                             run_len, K[r], table, dev_err, s, false, true,
-                                             opt && opt->merge_variant == MMS_MERGE_PARTITION),
+    st = check_launch(opt && opt->merge_variant == MMS_MERGE_PIPELINED
+                          ? mms::launch_merge_pipelined(8, false, comp[cur], comp[1 - cur],
+                                                        (long long)n, run_len, K[r], table, dev_err,
+                                                        s, true)
+                          : mms::launch_merge_pass(8, tw, S, false, comp[cur], comp[1 - cur],
+                                                   (long long)n, run_len, K[r], table, dev_err, s,
+                                                   false, true,
+                                                   opt && opt->merge_variant == MMS_MERGE_PARTITION),
                       "merge_pass");
     mark();
     cur = 1 - cur;
@@ -452,10 +464,11 @@ mms_status mms_sort_pairs_ex(mms_key_type kt, void* d_keys, uint32_t* d_values, 
   if (opt && opt->tile_items != 0 && opt->tile_items != 2048 && opt->tile_items != 4096)
     return fail(MMS_ERR_INVALID_ARG, "tile_items of a key-value sort must be 0, 2048 or 4096%s");
   if (opt && opt->test_flags != 0) return fail(MMS_ERR_INVALID_ARG, "test flags apply to mms_sort_keys_ex only%s");
-  if (opt && opt->merge_variant != MMS_MERGE_TREE && opt->merge_variant != MMS_MERGE_PARTITION)
-    return fail(MMS_ERR_INVALID_ARG, "merge_variant must be MMS_MERGE_TREE or MMS_MERGE_PARTITION%s");
-  if (opt && opt->merge_variant == MMS_MERGE_PARTITION && opt->tile_items != 0)
-    return fail(MMS_ERR_INVALID_ARG, "the partition merge variant takes the default tile geometry (tile_items 0)%s");
+  if (opt && opt->merge_variant != MMS_MERGE_TREE && opt->merge_variant != MMS_MERGE_PARTITION &&
+      opt->merge_variant != MMS_MERGE_PIPELINED)
+    return fail(MMS_ERR_INVALID_ARG, "merge_variant must be MMS_MERGE_TREE, MMS_MERGE_PARTITION or MMS_MERGE_PIPELINED%s");
+  if (opt && opt->merge_variant != MMS_MERGE_TREE && opt->tile_items != 0)
+    return fail(MMS_ERR_INVALID_ARG, "the partition and pipelined merge variants take the default tile geometry (tile_items 0)%s");
   const WsLayout L = ws_layout(kt, n, 1);
   cudaStream_t s = (cudaStream_t)stream;
   bool owned = false;
@@ -548,7 +561,7 @@ mms_status mms_splitter(mms_key_type kt, const void* d_in, size_t n, size_t run_
 
 static mms_status merge_pass_entry(mms_key_type kt, const void* d_in, void* d_out, size_t n,
                                    size_t run_len, int K, const int64_t* d_table, void* d_ws,
-                                   size_t ws_bytes, void* stream, bool partition) {
+                                   size_t ws_bytes, void* stream, int variant) {
   mms_status st = check_round_args(kt, run_len, K);
   if (st != MMS_OK) return st;
   if (n == 0) return MMS_OK;
@@ -562,25 +575,41 @@ static mms_status merge_pass_entry(mms_key_type kt, const void* d_in, void* d_ou
   if (d_ws && (ws_bytes < kStatusBytes || !aligned16(d_ws)))
     return fail(MMS_ERR_INVALID_ARG, "workspace too small or not 16-byte aligned%s");
   int* dev_err = d_ws ? static_cast<int*>(d_ws) : nullptr;
+  if (variant == MMS_MERGE_PIPELINED)
+    return check_launch(mms::launch_merge_pipelined((int)kb, false, d_in, d_out, (long long)n,
+                                                    (long long)run_len, K,
+                                                    reinterpret_cast<const long long*>(d_table),
+                                                    dev_err, (cudaStream_t)stream, false),
+                        "merge_pass");
   return check_launch(mms::launch_merge_pass((int)kb, mms::default_tile_warps((int)kb),
                                              1024ll * mms::default_tile_warps((int)kb), false, d_in,
                                              d_out, (long long)n,
                                              (long long)run_len, K,
                                              reinterpret_cast<const long long*>(d_table), dev_err,
-                                             (cudaStream_t)stream, false, false, partition),
+                                             (cudaStream_t)stream, false, false,
+                                             variant == MMS_MERGE_PARTITION),
                       "merge_pass");
 }
 
 mms_status mms_merge_pass(mms_key_type kt, const void* d_in, void* d_out, size_t n,
                           size_t run_len, int K, const int64_t* d_table, void* d_ws,
                           size_t ws_bytes, void* stream) {
-  return merge_pass_entry(kt, d_in, d_out, n, run_len, K, d_table, d_ws, ws_bytes, stream, false);
+  return merge_pass_entry(kt, d_in, d_out, n, run_len, K, d_table, d_ws, ws_bytes, stream,
+                          MMS_MERGE_TREE);
 }
 
 mms_status mms_merge_pass_partition(mms_key_type kt, const void* d_in, void* d_out, size_t n,
                                     size_t run_len, int K, const int64_t* d_table, void* d_ws,
                                     size_t ws_bytes, void* stream) {
-  return merge_pass_entry(kt, d_in, d_out, n, run_len, K, d_table, d_ws, ws_bytes, stream, true);
+  return merge_pass_entry(kt, d_in, d_out, n, run_len, K, d_table, d_ws, ws_bytes, stream,
+                          MMS_MERGE_PARTITION);
+}
+
+mms_status mms_merge_pass_pipelined(mms_key_type kt, const void* d_in, void* d_out, size_t n,
+                                    size_t run_len, int K, const int64_t* d_table, void* d_ws,
+                                    size_t ws_bytes, void* stream) {
+  return merge_pass_entry(kt, d_in, d_out, n, run_len, K, d_table, d_ws, ws_bytes, stream,
+                          MMS_MERGE_PIPELINED);
 }
 
 }  // extern "C"
