@@ -93,7 +93,7 @@ int tile_warps_for(int key_bytes, const mms_options* opt) {
 // its tree over those runs only, so it costs what a round of the next power
 // of two does.  Merge levels cost about the same for
 // K = 4..16, so the optimum first minimises the tree levels ceil(log2 runs)
-// and then the rounds (e.g. (8,8,8,8,4) for 10^8 4-byte keys).  The choice is
+// and then the rounds (e.g. (16,16,8,8) for 10^8 4-byte keys).  The choice is
 // a coin-change dynamic program over log2 of the coverage.  opt->fanout fixes
 // every round's K instead; the result does not depend on the plan.
 namespace plan_model {
