@@ -85,6 +85,7 @@ __global__ void __launch_bounds__((WARPS + 1) * 32, 2)
   if (warp == WARPS) {
     // Producer: plan and stage tile q into s(q) once tile q - 2 has released it.
     unsigned empty_par = 0u;                      // bit b: parity of the next wait on empty[b]
+    long long staged = 0;                         // tiles staged so far
     for (long long q = 0;; ++q) {
       const long long t = (long long)blockIdx.x + q * gridDim.x;
       if (t >= ntiles) break;
@@ -110,7 +111,17 @@ __global__ void __launch_bounds__((WARPS + 1) * 32, 2)
         if (ctl[kCtlNodeFields * 32 + 3]) mbar_arrive_plain(&full[b]);
         mbar_arrive_plain(&full[b]);              // publishes the node table and plain loads
       }
+      staged = q + 1;
     }
+    // Before the warp leaves, the copies it started have landed: the last two
+    // staged tiles are the only ones whose full phase the merging warps may not
+    // have awaited (if they stopped early), and no later staging reuses their
+    // buffers, so their parities are unambiguous.  Bounded, like every wait.
+    if (lane == 0) {
+      for (long long q = staged - 2; q < staged; ++q)
+        if (q >= 0) (void)mbar_wait_bounded(&full[(int)((3 - q % 3) % 3)], (unsigned)((q / 3) & 1));
+    }
+    __syncwarp();
     return;
   }
 
