@@ -153,6 +153,7 @@ __device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool ac
   Idx d = 0;                  // selected samples of this run at the current stride
   Item<KeyT> e{KeyT(0), false};  // the d-th sample (position d*s-1) when d >= 1
   const int T = 64 - __clzll((long long)k);
+  bool pad_prev = true;       // the previous level had a pad candidate (so e may be a pad)
   for (int lev = T; lev >= 1; --lev) {
     const int sh = lev - 1;                     // s2 = 2^sh
     const Idx kp = k >> sh;
@@ -160,6 +161,13 @@ __device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool ac
     Item<KeyT> o = load_item(run, rlen, ((dd + 1) << sh) - 1);
     Item<KeyT> z{KeyT(0), false};
     if (d >= 1) z = load_item(run, rlen, ((dd - 1) << sh) - 1);
+    // The largest selected item (lane mz's e) needs none of the new loads:
+    // its reduction overlaps them.  e is a pad only if the previous level had
+    // a pad candidate.
+    const bool hasZ = act && d >= 1;
+    const int mz = pad_prev ? grp_argmax(gm, hasZ, e) : grp_argmax_real(gm, hasZ, e.key);
+    Item<KeyT> zmax{KeyT(0), false};
+    if (mz >= 0) zmax = pad_prev ? shfl_item(gm, e, mz) : Item<KeyT>{__shfl_sync(gm, e.key, mz), false};
     // Pads at this level: o is a lane's highest position, so when no o is a
     // pad, no item of the level is (e, z and any deeper item lie below o).
     const bool any_pad = __any_sync(gm, act && o.pad);
@@ -170,16 +178,12 @@ __device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool ac
     Idx cnt = dd + 1;
 
     // Candidates above every selected item are dropped first, in one step.
-    const bool hasZ = act && d >= 1;
-    const int mz = any_pad ? grp_argmax(gm, hasZ, e) : grp_argmax_real(gm, hasZ, e.key);
     bool above = act;
     if (mz >= 0) {
       if (any_pad) {
-        const Item<KeyT> zmax = shfl_item(gm, e, mz);
         above = act && (lane == mz || before_cross(zmax, mz, o, lane));
       } else {                                  // no pads: keys, then runs
-        const KeyT zk = __shfl_sync(gm, e.key, mz);
-        above = act && (lane == mz || zk < o.key || (zk == o.key && mz < lane));
+        above = act && (lane == mz || zmax.key < o.key || (zmax.key == o.key && mz < lane));
       }
     }
     const unsigned abovem = __ballot_sync(gm, above);
@@ -230,6 +234,7 @@ __device__ __forceinline__ Idx multiseq_pivot(const KeyT* run, Idx rlen, bool ac
     }
     d = cnt;
     e = top;
+    pad_prev = any_pad;
   }
   return d;
 }
