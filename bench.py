@@ -44,6 +44,9 @@ def parse():
     p.add_argument("--n", type=int, default=DEFAULT_N)
     p.add_argument("--fanout", type=int, default=0, help="merge fanout K (0 = planner)")
     p.add_argument("--tile", type=int, default=0, help="tile items (0 = library default)")
+    p.add_argument("--base-items", type=int, default=0,
+                   help="length of the base case's sorted runs (0 = library default, one CTA tile; "
+                        "16384 / 32768 / 65536 for 4-byte keys: one cluster of 2 / 4 / 8 CTAs per run)")
     p.add_argument("--pairs", action="store_true", help="key + uint32 index payload (stable key-value sort)")
     p.add_argument("--merge-variant", default="tree", choices=["tree", "partition", "pipelined"],
                    help="merge rounds: the CTA merge tree (default), the heap-free partition variant or "
@@ -243,6 +246,8 @@ def hbm_peak() -> float:
 KERNEL_SOURCES = {
     "merge_pass_kernel": ["merge_pass.cu", "merge_tile.cuh", "mms_common.cuh", "mms_kernels.cuh"],
     "tile_sort_kernel": ["tile_sort.cu", "tile_sort.cuh", "mms_common.cuh", "mms_kernels.cuh"],
+    "tile_sort_cluster_kernel": ["tile_sort_cluster.cu", "tile_sort.cuh", "mms_common.cuh",
+                                 "mms_kernels.cuh"],
 }
 
 
@@ -773,7 +778,7 @@ def run_sweep(args):
                 split_r = [statistics.mean(x[1 + 2 * r] for x in st) for r in range(len(plan))]
                 split = sum(split_r)
                 # runs merged per group in each round: K, except in a last round with fewer runs left
-                runs = -(-n // mms.tile_items(kt))
+                runs = -(-n // mms.base_run_items(kt, n))
                 merged = []
                 for k in plan:
                     merged.append(min(k, runs))
@@ -830,7 +835,11 @@ def main():
     vals = torch.empty(N, dtype=torch.int32, device=dev)
     iota32 = torch.arange(N, dtype=torch.int32, device=dev)
     ws = torch.zeros(mms.workspace_bytes(kt, N, args.pairs), dtype=torch.uint8, device=dev)
-    plan = mms.plan(kt, N, args.fanout, args.tile, pairs=args.pairs)
+    base_items = 0 if args.pairs else args.base_items
+    plan = mms.plan(kt, N, args.fanout, args.tile, pairs=args.pairs, base_items=base_items)
+    base_run = (mms.base_run_items(mms.KEY_U64, N, args.tile) if args.pairs
+                else mms.base_run_items(kt, N, args.tile, base_items))
+    base_kernel = "tile_sort_kernel" if base_run == (args.tile or mms.tile_items(kt)) else "tile_sort_cluster_kernel"
     n_ev = 2 + 2 * len(plan) + (1 if args.pairs else 0)
     stream = torch.cuda.current_stream()
     mv = {"partition": mms.MERGE_PARTITION, "pipelined": mms.MERGE_PIPELINED}.get(args.merge_variant,
@@ -847,7 +856,7 @@ def main():
                            tile_items=args.tile, merge_variant=mv)
         else:
             mms.sort_keys(work, fanout=args.fanout, workspace=ws, kt=kt, events=events,
-                          tile_items=args.tile, merge_variant=mv)
+                          tile_items=args.tile, merge_variant=mv, base_items=base_items)
         if bounds:
             bounds[1].record(stream)
 
@@ -946,7 +955,7 @@ def main():
                 "per_pass_frac": [bytes_pass / (m / 1e3) / 1e9 / peak for m in merge_ms],
                 "tile_sort_frac": bytes_pass / (tile_ms / 1e3) / 1e9 / peak}
     if headline:
-        roofline["tile_sort_traffic"] = load_traffic(N, "tile_sort_kernel")
+        roofline["tile_sort_traffic"] = load_traffic(N, base_kernel)
 
     out = {
         "metric": METRIC if headline else (f"Gkeys/s at {N} {args.key}" + (" pairs" if args.pairs else "")
@@ -959,6 +968,7 @@ def main():
                                + ", one sort per step",
                    "global_batch": N * world, "seq_len": None, "parallelism": f"replicas{world}",
                    "plan_fanouts": plan, "tile": args.tile or mms.tile_items(kt),
+                   "base_run": base_run, "base_kernel": base_kernel,
                    "merge_variant": args.merge_variant, "seed": args.seed + rank,
                    "l2": f"input {N * kb / 1e6:.0f} MB > 129 MB L2; a device copy restores the input "
                          "before every step, outside the timed events" if N * kb > 129e6 else
@@ -987,12 +997,12 @@ def main():
     by_k = {}
     if headline or partition_run:
         for kf in ((2, 4) if headline else (2, 4, 8, 16)):
-            planf = mms.plan(kt, N, kf, args.tile)
+            planf = mms.plan(kt, N, kf, args.tile, base_items=base_items)
             nf = 2 + 2 * len(planf)
             evf = [[torch.cuda.Event(enable_timing=True) for _ in range(nf)] for _ in range(10)]
             for i in range(13):
                 work.copy_(src)
-                mms.sort_keys(work, fanout=kf, workspace=ws, kt=kt, tile_items=args.tile,
+                mms.sort_keys(work, fanout=kf, workspace=ws, kt=kt, tile_items=args.tile, base_items=base_items,
                               events=evf[i - 3] if i >= 3 else None, merge_variant=mv)
             torch.cuda.synchronize()
             # merge pass of round r: from event 2 + 2r (after its splitter) to 3 + 2r
@@ -1035,7 +1045,7 @@ def main():
             with torch.cuda.stream(comp):
                 comp.wait_event(loaded)
                 mms.sort_keys(bufs[j], fanout=args.fanout, workspace=ws, kt=mms.KEY_U32,
-                              tile_items=args.tile, stream=comp)
+                              tile_items=args.tile, stream=comp, base_items=args.base_items)
                 sorted_.record(comp)
             with torch.cuda.stream(down):
                 down.wait_event(sorted_)
@@ -1074,7 +1084,7 @@ def main():
             with torch.cuda.stream(comp):
                 bufs[0].copy_(h_in, non_blocking=True)
                 mms.sort_keys(bufs[0], fanout=args.fanout, workspace=ws, kt=mms.KEY_U32,
-                              tile_items=args.tile, stream=comp)
+                              tile_items=args.tile, stream=comp, base_items=args.base_items)
                 outs[0].copy_(bufs[0], non_blocking=True)
             b.record(comp)
             torch.cuda.synchronize()

@@ -65,8 +65,9 @@ typedef struct {
                         `stream` before the first kernel, events[i] after the i-th kernel
                         (base case, then splitter and merge pass of each round), while
                         i < num_events.  Lets a caller time every step of the real call. */
-  int tile_items;    /* base-case / merge tile: 0 = mms_tile_items(kt); else 4096 or 8192
-                        for 4-byte keys, 2048 or 4096 for 8-byte keys */
+  int tile_items;    /* CTA tile of the base case and of the merge rounds: 0 =
+                        mms_tile_items(kt); else 4096 or 8192 for 4-byte keys, 2048 or
+                        4096 for 8-byte keys (the base case's runs: base_items) */
   int merge_tile_items; /* output tile of the merge rounds: 0 = tile_items; else a multiple
                         of 1024 from 4096 (2048 for 8-byte keys) up to tile_items */
   int test_flags;    /* test hooks, 0 in normal use.  MMS_TEST_STAGING_TIMEOUT: every merge
@@ -86,6 +87,14 @@ typedef struct {
                         current one.  Same results; the variants take the default tile
                         geometry only (tile_items and merge_tile_items 0), apply to
                         mms_sort_keys_ex and mms_sort_pairs_ex, and take no test flags. */
+  int base_items;    /* length of the sorted runs the base case of mms_sort_keys_ex
+                        produces (Sec. 4.3): 0 = the tile (one CTA per tile, the
+                        default); for 4-byte keys at the 8192-key tile also 16384,
+                        32768 or 65536 = one thread-block cluster of 2, 4 or 8 CTAs per
+                        run, which sorts 8192 keys per CTA and merges them across the
+                        cluster's shared memory.  Longer runs leave fewer merge levels
+                        to the rounds (same results).  A key-value sort takes 0 or its
+                        composite tile. */
 } mms_options;
 
 #define MMS_TEST_STAGING_TIMEOUT 1
@@ -144,6 +153,11 @@ mms_status mms_stream_status(void* stream);
 /* Items per base-case tile and per merge output tile for key type kt
  * (8192 for 4-byte keys, 4096 for 8-byte keys). */
 size_t mms_tile_items(mms_key_type kt);
+
+/* Length of the sorted runs the base case of mms_sort_keys_ex produces for n
+ * keys of type kt under opt (NULL: defaults): the tile (tile_items, default
+ * mms_tile_items(kt)) or opt->base_items.  0 for an invalid kt or opt. */
+size_t mms_base_run_items(mms_key_type kt, size_t n, const mms_options* opt);
 
 /* Plan of a sort: number of merge rounds and the fanout of each (up to 16
  * entries written to fanouts).  Returns the number of rounds. */

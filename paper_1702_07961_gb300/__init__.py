@@ -17,7 +17,7 @@ import os
 import threading
 
 __all__ = ["load", "KEY_U32", "KEY_U64", "KEY_F32", "key_type_of", "sort_keys", "sort_pairs",
-           "workspace_bytes", "tile_items", "plan", "tile_sort", "splitter_rows", "splitter",
+           "workspace_bytes", "tile_items", "base_run_items", "plan", "tile_sort", "splitter_rows", "splitter",
            "merge_pass", "workspace_status", "stream_status", "MMSError", "sort_keys_noalloc",
            "noalloc_status", "NOALLOC_MAX_KEYS", "TEST_STAGING_TIMEOUT",
            "segmented_workspace_bytes", "segmented_rounds", "segmented_sort", "SegmentedGraph"]
@@ -41,7 +41,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("fanout", ctypes.c_int), ("num_events", ctypes.c_int),
                 ("events", ctypes.POINTER(ctypes.c_void_p)), ("tile_items", ctypes.c_int),
                 ("merge_tile_items", ctypes.c_int), ("test_flags", ctypes.c_int),
-                ("merge_variant", ctypes.c_int)]
+                ("merge_variant", ctypes.c_int), ("base_items", ctypes.c_int)]
 
 
 # mms_options.test_flags: a test hook that makes every merge CTA's extra
@@ -91,6 +91,8 @@ def load() -> ctypes.CDLL:
         L.mms_noalloc_status.restype = i32
         L.mms_tile_items.argtypes = [i32]
         L.mms_tile_items.restype = sz
+        L.mms_base_run_items.argtypes = [i32, sz, ctypes.POINTER(_Options)]
+        L.mms_base_run_items.restype = sz
         L.mms_plan.argtypes = [i32, sz, ctypes.POINTER(_Options), ctypes.POINTER(ctypes.c_int), i32]
         L.mms_plan.restype = i32
         L.mms_tile_sort.argtypes = [i32, vp, vp, sz, vp]
@@ -158,9 +160,10 @@ def _ptr(t):
 
 
 def _opts(fanout: int, events=None, stream=None, tile_items: int = 0, merge_tile_items: int = 0,
-          test_flags: int = 0, merge_variant: int = 0):
+          test_flags: int = 0, merge_variant: int = 0, base_items: int = 0):
     o = _Options()
     o.fanout = int(fanout)
+    o.base_items = int(base_items)
     o.tile_items = int(tile_items)
     o.merge_tile_items = int(merge_tile_items)
     o.test_flags = int(test_flags)
@@ -184,32 +187,42 @@ def tile_items(kt: int) -> int:
     return int(load().mms_tile_items(kt))
 
 
-def plan(kt: int, n: int, fanout: int = 0, tile_items: int = 0, pairs: bool = False):
+def base_run_items(kt: int, n: int, tile_items: int = 0, base_items: int = 0) -> int:
+    """Length of the sorted runs the base case of a keys-only sort of n keys produces."""
+    o = _opts(0, tile_items=tile_items, base_items=base_items)
+    return int(load().mms_base_run_items(kt, n, ctypes.byref(o)))
+
+
+def plan(kt: int, n: int, fanout: int = 0, tile_items: int = 0, pairs: bool = False,
+         base_items: int = 0):
     """Fanout of every merge round of a sort of n keys (of n pairs when `pairs`:
     the rounds of a key-value sort run on 8-byte composites)."""
     if pairs:
         kt = KEY_U64
     buf = (ctypes.c_int * 64)()
-    o = _opts(fanout, tile_items=tile_items)
+    o = _opts(fanout, tile_items=tile_items, base_items=base_items)
     r = load().mms_plan(kt, n, ctypes.byref(o), buf, 64)
     return [buf[i] for i in range(r)]
 
 
 def sort_keys(keys, fanout: int = 0, workspace=None, stream=None, kt: int | None = None, events=None,
               tile_items: int = 0, merge_tile_items: int = 0, test_flags: int = 0,
-              merge_variant: int = MERGE_TREE):
+              merge_variant: int = MERGE_TREE, base_items: int = 0):
     """Sorts a contiguous CUDA tensor of keys in place; returns it.
 
     ``events``: optional list of ``torch.cuda.Event(enable_timing=True)``; the
     library records them before the first kernel and after each kernel.
     ``test_flags``: test hooks (``TEST_STAGING_TIMEOUT``), 0 in normal use.
     ``merge_variant``: ``MERGE_TREE``, ``MERGE_PARTITION`` or ``MERGE_PIPELINED``.
+    ``base_items``: length of the base case's sorted runs (0: the library's
+    default, ``base_run_items``).
     """
     assert keys.is_cuda and keys.is_contiguous()
     kt = key_type_of(keys) if kt is None else kt
     n = keys.numel()
     ws_ptr, ws_len = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
-    o = _opts(fanout, events, stream, tile_items, merge_tile_items, test_flags, merge_variant)
+    o = _opts(fanout, events, stream, tile_items, merge_tile_items, test_flags, merge_variant,
+              base_items)
     _check(load().mms_sort_keys_ex(kt, _ptr(keys), n, ws_ptr, ws_len, _stream_handle(stream), ctypes.byref(o)))
     return keys
 

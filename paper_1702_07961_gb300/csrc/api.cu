@@ -83,6 +83,28 @@ int tile_warps_for(int key_bytes, const mms_options* opt) {
   return mms::default_tile_warps(key_bytes);
 }
 
+// Length of the sorted runs the base case of a keys-only sort produces: one
+// CTA tile by default, or the caller's mms_options.base_items (for 4-byte keys
+// also one thread-block cluster of 2, 4 or 8 tiles per run).  Runs of one tile
+// are the default because on GB300 a cluster merge level (co-ranks and copies
+// through distributed shared memory between two cluster barriers) measured
+// dearer than the merge-round level it saves: 10^8 u32 keys sorted at 37.1
+// Gkeys/s from runs of 8192, 36.5 / 35.0 / 33.7 from runs of 16384 / 32768 /
+// 65536 (base case 0.605 -> 0.779 / 0.995 / 1.309 ms).
+long long base_run_items(int key_bytes, size_t n, const mms_options* opt) {
+  (void)n;
+  const long long T = 1024ll * tile_warps_for(key_bytes, opt);
+  if (opt && opt->base_items > 0) return opt->base_items;
+  return T;
+}
+
+// Whether base_items is a run length the keys-only base case can produce.
+bool valid_base_items(int key_bytes, int tw, int base_items) {
+  if (base_items == 0 || base_items == 1024 * tw) return true;
+  if (key_bytes != 4 || tw != mms::default_tile_warps(4)) return false;
+  return base_items == 2 * 1024 * tw || base_items == 4 * 1024 * tw || base_items == 8 * 1024 * tw;
+}
+
 // Fanouts of the merge rounds.  Sec. 6.2 tunes K per platform by
 // measurement; here the planner picks, per sort, the sequence of power-of-two
 // fanouts that minimises a cost model measured on GB300.  A round of fanout K
@@ -104,7 +126,7 @@ constexpr double kLaunchMs = 0.010;                                 // two launc
 }  // namespace plan_model
 
 int plan_rounds(int key_bytes, size_t n, const mms_options* opt, int* K, int maxr) {
-  const long long S = 1024ll * tile_warps_for(key_bytes, opt);
+  const long long S = base_run_items(key_bytes, n, opt);
   const long long runs = ((long long)n + S - 1) / S;
   if (runs <= 1) return 0;
   if (opt && opt->fanout >= 2) {
@@ -259,6 +281,15 @@ size_t mms_tile_items(mms_key_type kt) {
   return valid_kt(kt) ? (size_t)1024 * mms::default_tile_warps(key_bytes_of(kt)) : 0;
 }
 
+size_t mms_base_run_items(mms_key_type kt, size_t n, const mms_options* opt) {
+  if (!valid_kt(kt)) return 0;
+  const int kb = key_bytes_of(kt);
+  if (opt && (opt->tile_items != 0 && !mms::valid_tile_warps(kb, opt->tile_items / 1024)))
+    return 0;
+  if (opt && !valid_base_items(kb, tile_warps_for(kb, opt), opt->base_items)) return 0;
+  return (size_t)base_run_items(kb, n, opt);
+}
+
 size_t mms_sort_workspace_bytes(mms_key_type kt, size_t n, int with_values) {
   if (!valid_kt(kt)) return 0;
   return ws_layout(kt, n, with_values).total;
@@ -314,6 +345,8 @@ mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws,
     return fail(MMS_ERR_INVALID_ARG, "tile_items must be 0, 4096/8192 (4-byte keys) or 2048/4096 (8-byte keys)%s");
   const int tw = tile_warps_for(kb, opt);
   const long long S = 1024ll * tw;
+  if (opt && !valid_base_items(kb, tw, opt->base_items))
+    return fail(MMS_ERR_INVALID_ARG, "base_items must be 0, tile_items, or 2, 4 or 8 times the 8192-key tile (4-byte keys)%s");
   if (opt && opt->merge_tile_items != 0 &&
       (opt->merge_tile_items % 1024 != 0 || opt->merge_tile_items < (kb == 8 ? 2048 : 4096) ||
        opt->merge_tile_items > S))
@@ -358,10 +391,17 @@ mms_status mms_sort_keys_ex(mms_key_type kt, void* d_keys, size_t n, void* d_ws,
     ++ev;
   };
   mark();
-  st = check_launch(mms::launch_tile_sort(kb, tw, is_f32, is_f32 && rounds == 0, d_keys, cur,
-                                          (long long)n, s), "tile_sort");
+  // The base case: one CTA per tile, or one thread-block cluster per run of
+  // several tiles.
+  long long run_len = base_run_items(kb, n, opt);
+  st = check_launch(run_len == S
+                        ? mms::launch_tile_sort(kb, tw, is_f32, is_f32 && rounds == 0, d_keys, cur,
+                                                (long long)n, s)
+                        : mms::launch_tile_sort_cluster((int)(run_len / S), is_f32,
+                                                        is_f32 && rounds == 0, d_keys, cur,
+                                                        (long long)n, s),
+                    "tile_sort");
   mark();
-  long long run_len = S;
   for (int r = 0; r < rounds && st == MMS_OK; ++r) {
     const long long Sm = merge_tile_for(kb, tw, K[r], opt, n, run_len);
     st = check_launch(mms::launch_splitter(kb, Sm, cur, (long long)n, run_len, K[r], table, s, true),
@@ -407,6 +447,7 @@ static mms_status pairs32_run(bool is_f32, void* d_keys, uint32_t* d_values, siz
   if (opt) o8 = *opt;
   const int tw = (opt && opt->tile_items) ? opt->tile_items / 1024 : mms::default_tile_warps(8);
   o8.tile_items = 1024 * tw;
+  o8.base_items = 0;                    // one CTA per composite tile
   const long long S = 1024ll * tw;
   int K[64];
   const int rounds = plan_rounds(8, n, &o8, K, 64);
@@ -464,6 +505,8 @@ mms_status mms_sort_pairs_ex(mms_key_type kt, void* d_keys, uint32_t* d_values, 
   if (opt && opt->tile_items != 0 && opt->tile_items != 2048 && opt->tile_items != 4096)
     return fail(MMS_ERR_INVALID_ARG, "tile_items of a key-value sort must be 0, 2048 or 4096%s");
   if (opt && opt->test_flags != 0) return fail(MMS_ERR_INVALID_ARG, "test flags apply to mms_sort_keys_ex only%s");
+  if (opt && opt->base_items != 0 && opt->base_items != (opt->tile_items ? opt->tile_items : 4096))
+    return fail(MMS_ERR_INVALID_ARG, "base_items of a key-value sort must be 0 or its composite tile%s");
   if (opt && opt->merge_variant != MMS_MERGE_TREE && opt->merge_variant != MMS_MERGE_PARTITION &&
       opt->merge_variant != MMS_MERGE_PIPELINED)
     return fail(MMS_ERR_INVALID_ARG, "merge_variant must be MMS_MERGE_TREE, MMS_MERGE_PARTITION or MMS_MERGE_PIPELINED%s");

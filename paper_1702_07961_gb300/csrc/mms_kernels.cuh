@@ -58,6 +58,13 @@ size_t merge_pass_smem_bytes(int key_bytes, int warps, int K);
 cudaError_t launch_tile_sort(int key_bytes, int tile_warps, bool xin, bool xout, const void* in,
                              void* out, long long n, cudaStream_t s);
 
+// Base case over runs of cluster_ctas * 8192 4-byte keys (cluster_ctas 2, 4
+// or 8): one thread-block cluster per run, each CTA sorting one 8192-key tile,
+// then log2(cluster_ctas) merge levels across the cluster's shared memory.
+// in == out allowed.
+cudaError_t launch_tile_sort_cluster(int cluster_ctas, bool xin, bool xout, const void* in,
+                                     void* out, long long n, cudaStream_t s);
+
 // Base case of the key-value sort: 32-bit keys -> sorted tiles of 64-bit
 // composites (ordered key << 32 | array position).
 cudaError_t launch_tile_sort_composite(int tile_warps, bool xin, const void* keys32, void* out64,

@@ -135,11 +135,13 @@ __device__ __forceinline__ void cta_store_tile(const KeyT* src, KeyT* dst, int m
   for (int i = body + (int)threadIdx.x; i < m; i += blockDim.x) dst[i] = src[i];
 }
 
-// Everything after the load: warp sorts, CTA merge levels, store of the tile.
+// Everything after the load up to the sorted tile in shared memory: warp
+// sorts, then the CTA merge levels.  Returns the buffer (bufX or bufY of
+// smem_raw) that holds the tile's keys in order; its first min(T, n - base)
+// entries are the tile's.  xout: write the last level's output as floats.
 template <typename KeyT, int WARPS>
-__device__ __forceinline__ void tile_sort_finish(KeyT (&v)[32], KeyT* out, long long n,
-                                                 long long base, bool xout,
-                                                 unsigned char* smem_raw) {
+__device__ __forceinline__ KeyT* tile_sort_smem(KeyT (&v)[32], long long n, long long base,
+                                                bool xout, unsigned char* smem_raw) {
   constexpr int T = WARPS * kBlockItems;
   KeyT* bufX = reinterpret_cast<KeyT*>(smem_raw);
   KeyT* bufY = bufX + T + kTileSlack;
@@ -149,12 +151,9 @@ __device__ __forceinline__ void tile_sort_finish(KeyT (&v)[32], KeyT* out, long 
   // before the warps use it as transpose scratch.
   __syncthreads();
   warp_sort_1024(v, bufX + warp * kBlockItems, lane);
-  const long long trem = n - base;
-  const int m = trem >= T ? T : (int)trem;
   if constexpr (WARPS == 1) {
     warp_store_block<KeyT>(bufX, kBlockItems, v, lane, xout);
-    cta_store_tile(bufX, out + base, m);
-    return;
+    return bufX;
   }
   warp_store_block<KeyT>(bufX + warp * kBlockItems, kBlockItems, v, lane, false);
   __syncthreads();
@@ -179,15 +178,27 @@ __device__ __forceinline__ void tile_sort_finish(KeyT (&v)[32], KeyT* out, long 
     src = dst;
     dst = t;
   }
-  cta_store_tile(src, out + base, m);
+  return src;
 }
 
-// Sorts the tile of 1024 * WARPS keys of in[0, n) that starts at `base` into
-// the same positions of out (in == out allowed): the CTA body of the base case.
+// Everything after the load: the sort in shared memory and the store of the tile.
+template <typename KeyT, int WARPS>
+__device__ __forceinline__ void tile_sort_finish(KeyT (&v)[32], KeyT* out, long long n,
+                                                 long long base, bool xout,
+                                                 unsigned char* smem_raw) {
+  constexpr int T = WARPS * kBlockItems;
+  KeyT* res = tile_sort_smem<KeyT, WARPS>(v, n, base, xout, smem_raw);
+  const long long trem = n - base;
+  const int m = trem >= T ? T : (int)trem;
+  cta_store_tile(res, out + base, m);
+}
+
+// Loads this warp's 1024 keys of the tile of 1024 * WARPS keys that starts at
+// `base` (32 per lane, any assignment; pads past n), through the float order
+// transform when XIN.
 template <typename KeyT, int WARPS, bool XIN>
-__device__ __forceinline__ void tile_sort_tile(const KeyT* __restrict__ in, KeyT* out, long long n,
-                                               long long base, bool xout,
-                                               unsigned char* smem_raw) {
+__device__ __forceinline__ void tile_load(const KeyT* __restrict__ in, long long n, long long base,
+                                          KeyT (&v)[32]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long wbase = base + (long long)warp * kBlockItems;
   const long long rem = n - wbase;
@@ -195,7 +206,6 @@ __device__ __forceinline__ void tile_sort_tile(const KeyT* __restrict__ in, KeyT
 
   using V = Vec16<KeyT>;
   constexpr int NV = 32 / V::E;          // 16-byte vectors per lane
-  KeyT v[32];
   if (cnt == kBlockItems && ((uintptr_t)(in + wbase) & 15u) == 0) {
     const typename V::T* src = reinterpret_cast<const typename V::T*>(in + wbase);
 #pragma unroll
@@ -216,6 +226,16 @@ __device__ __forceinline__ void tile_sort_tile(const KeyT* __restrict__ in, KeyT
       }
     }
   }
+}
+
+// Sorts the tile of 1024 * WARPS keys of in[0, n) that starts at `base` into
+// the same positions of out (in == out allowed): the CTA body of the base case.
+template <typename KeyT, int WARPS, bool XIN>
+__device__ __forceinline__ void tile_sort_tile(const KeyT* __restrict__ in, KeyT* out, long long n,
+                                               long long base, bool xout,
+                                               unsigned char* smem_raw) {
+  KeyT v[32];
+  tile_load<KeyT, WARPS, XIN>(in, n, base, v);
   tile_sort_finish<KeyT, WARPS>(v, out, n, base, xout, smem_raw);
 }
 

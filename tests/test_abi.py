@@ -44,22 +44,41 @@ def test_tile_geometry(lib):
     assert mms.tile_items(mms.KEY_U64) == 4096
 
 
-def test_planner_round_count_is_ceil_log_k():
-    """ceil(log_K(N / tile)) merge rounds (Sec. 6.2)."""
+@pytest.mark.parametrize("base", [0, 8192, 16384, 65536])
+def test_planner_round_count_is_ceil_log_k(base):
+    """ceil(log_K(N / run)) merge rounds (Sec. 6.2), run = the base case's runs."""
     import math
     import paper_1702_07961_gb300 as mms
     for n in [1, 8192, 8193, 10**6, 10**8, 2**28]:
-        runs = -(-n // 8192)
+        run = mms.base_run_items(mms.KEY_U32, n, base_items=base)
+        assert run == (base or 8192)
+        runs = -(-n // run)
         for K in [2, 4, 8, 16, 32]:
             want = 0 if runs <= 1 else math.ceil(math.log(runs) / math.log(K) - 1e-12)
-            got = mms.plan(mms.KEY_U32, n, K)
+            got = mms.plan(mms.KEY_U32, n, K, base_items=base)
             assert len(got) == want and all(k == K for k in got)
-        auto = mms.plan(mms.KEY_U32, n)
+        auto = mms.plan(mms.KEY_U32, n, base_items=base)
         prod = 1
         for k in auto:
             assert 2 <= k <= 32
             prod *= k
         assert prod >= runs and (not auto or prod // min(auto) < runs)
+
+
+def test_base_run_items(lib):
+    """Runs of the base case: one CTA tile by default, 2, 4 or 8 tiles (a
+    cluster) on request for 4-byte keys; invalid settings give 0."""
+    import paper_1702_07961_gb300 as mms
+    assert mms.base_run_items(mms.KEY_U32, 10**8) == 8192
+    assert mms.base_run_items(mms.KEY_F32, 8193) == 8192
+    assert mms.base_run_items(mms.KEY_U64, 10**8) == 4096
+    assert mms.base_run_items(mms.KEY_U32, 10**8, tile_items=4096) == 4096
+    assert mms.base_run_items(mms.KEY_U32, 10**8, tile_items=8192, base_items=32768) == 32768
+    assert mms.base_run_items(mms.KEY_F32, 10**8, base_items=16384) == 16384
+    assert mms.base_run_items(mms.KEY_U32, 10**8, base_items=65536) == 65536
+    assert mms.base_run_items(mms.KEY_U32, 10**8, base_items=12288) == 0
+    assert mms.base_run_items(mms.KEY_U64, 10**8, base_items=16384) == 0
+    assert mms.base_run_items(mms.KEY_U32, 10**8, tile_items=4096, base_items=32768) == 0
 
 
 def test_workspace_grows_with_n(lib):
