@@ -97,3 +97,19 @@ def test_offset_slice_and_workspace(gpu):
     gpu.sort_keys(sl, workspace=ws, kt=gpu.KEY_U32, base_items=32768)
     gpu.workspace_status(ws)
     assert_bits_equal(to_host(sl, np.uint32), oracle.sort(keys)[0])
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("base", [16384, 32768, 65536])
+def test_full_size_permutation_1e8(gpu, base):
+    """The bench workload (a uniform permutation of 0..10^8-1) sorted from
+    cluster runs must give iota."""
+    import torch
+    n = 10**8
+    t = to_dev(synth.permutation(n, 1))
+    gpu.sort_keys(t, kt=gpu.KEY_U32, base_items=base)
+    step = 1 << 26
+    for a in range(0, n, step):
+        b = min(n, a + step)
+        want = torch.arange(a, b, dtype=torch.int64, device=t.device)
+        assert torch.equal(t[a:b].to(torch.int64) & 0xFFFFFFFF, want)
