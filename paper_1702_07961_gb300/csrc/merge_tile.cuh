@@ -103,11 +103,17 @@ __device__ __forceinline__ void merge_tile_pivots(long long n, long long run_len
 // barrier publishes the plain loads and the table, the barrier's phase the
 // copies.  On segment bounds that fail their check, ctl's error scalar is set
 // and nothing is staged.
+// `part` splits the work between two warps that both call this with the same
+// bounds: bit 0 stages the segments (and writes the tile size and error
+// scalars), bit 1 writes the node table (and the level and node counts).  The
+// two halves need only the segment lengths and spans, which both compute, so a
+// CTA can start the copies and build the table at the same time.
 template <typename KeyT, int WARPS>
 __device__ __forceinline__ void merge_plan_warp(const KeyT* __restrict__ in, long long n,
                                                 long long run_len, int K, long long g,
                                                 long long j, long long lo, long long hi, int S,
-                                                KeyT* stage, int* ctl, uint64_t* bar, int lane) {
+                                                KeyT* stage, int* ctl, uint64_t* bar, int lane,
+                                                int part = 3) {
   using G = MergeGeom<KeyT, WARPS>;
   constexpr int E = G::E;
   const long long gstart = g * run_len * K;
@@ -126,7 +132,7 @@ __device__ __forceinline__ void merge_plan_warp(const KeyT* __restrict__ in, lon
   const int sum = (int)__reduce_add_sync(0xffffffffu, (unsigned)len32);
   const bool bad = __any_sync(0xffffffffu, bad_seg) || sum != want || K > kMaxFanout || K < 2 ||
                    S > G::S || S < kBlockItems || (smem_u32addr(stage) & 15u) != 0;
-  if (lane == 0) {
+  if (lane == 0 && (part & 1)) {
     ctl[kCtlNodeFields * 32 + 2] = (int)want;
     ctl[kCtlNodeFields * 32 + 3] = bad ? 1 : 0;
   }
@@ -175,11 +181,14 @@ __device__ __forceinline__ void merge_plan_warp(const KeyT* __restrict__ in, lon
         if (e < s_src + s_len) stage[s_off + (int)(e - s_src)] = in[e];
       }
     };
-    const unsigned total = __reduce_add_sync(0xffffffffu, bulk_bytes);
-    if (lane == 0) mbar_arrive_expect_tx(bar, total);
-    __syncwarp();
-    if (bulk_bytes) bulk_g2s(stage + R, in + bulk_lo, bulk_bytes, bar);
-    if (__any_sync(0xffffffffu, act && len > 0 && bulk_hi < gsrc + len)) plain_tail();
+    if (part & 1) {
+      const unsigned total = __reduce_add_sync(0xffffffffu, bulk_bytes);
+      if (lane == 0) mbar_arrive_expect_tx(bar, total);
+      __syncwarp();
+      if (bulk_bytes) bulk_g2s(stage + R, in + bulk_lo, bulk_bytes, bar);
+      if (__any_sync(0xffffffffu, act && len > 0 && bulk_hi < gsrc + len)) plain_tail();
+    }
+    if (!(part & 2)) return;
     // Merge-tree nodes, one per lane, in level order: node (level l >= 1,
     // pair q) merges child A = segments [q*2^l, q*2^l + 2^(l-1)) and child
     // B = the rest of [q*2^l, (q+1)*2^l) (segments past the group's runs are
@@ -519,13 +528,14 @@ __device__ __forceinline__ bool merge_tile(const KeyT* __restrict__ in, KeyT* __
   int* ctl = reinterpret_cast<int*>(bar + 2);          // node table and scalars (see above)
   // Every thread is past the previous tile (whose store has read its shared
   // memory) before the staging copies overwrite the buffer.
+  // Warp 0 stages the segments while warp 1 builds the node table.
   long long lo = 0, hi = 0;
-  if ((threadIdx.x >> 5) == 0)
+  if ((threadIdx.x >> 5) < 2)
     merge_tile_pivots(n, run_len, K, g, j, lo_row, hi_row, S, threadIdx.x & 31, lo, hi);
   __syncthreads();
-  if ((threadIdx.x >> 5) == 0)
+  if ((threadIdx.x >> 5) < 2)
     merge_plan_warp<KeyT, WARPS>(in, n, run_len, K, g, j, lo, hi, S, bufX, ctl, bar,
-                                 threadIdx.x & 31);
+                                 threadIdx.x & 31, (threadIdx.x >> 5) == 0 ? 1 : 2);
   __syncthreads();
   if (ctl[kCtlNodeFields * 32 + 3] || (smem_u32addr(smem_raw) & 1023u) != 0) {
     if (threadIdx.x == 0) set_device_error(dev_err, kDevErrInternal);
